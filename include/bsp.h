@@ -1,0 +1,157 @@
+/*
+ * bsp.h -- C ABI of libbsp, a GB300 (sm_103a) implementation of the FFT
+ * bispectrum-multipole estimator and its modal variant from Regan,
+ * "An Inventory of Bispectrum Estimators for Redshift Space Distortions"
+ * (arXiv:1708.05303).
+ *
+ * Problem statement (Sec. 3.1, Eq. Standard_ell_Estim and
+ * Eq. Bisp_ell_restrict): given a gridded redshift-space density delta(k)
+ * in a periodic box of volume V, k-shells [k +- dk/2] and even multipoles
+ * l, return for every triangle bin (a, b, c), a >= b >= c,
+ *
+ *   B^l_abc = sum_{q1 in a, q2 in b, q3 in c, q1+q2+q3 = 0}
+ *             w_l(mu_1) delta(q1) delta(q2) delta(q3) / (V N_abc),
+ *
+ * w_l(mu) = (2l+1) L_l(mu), mu_1 the cosine between q1 and the line of
+ * sight z, N_abc the number of grid triangles in the bin (V_B of Sec. 3.1).
+ * The Legendre leg is the largest shell a.  The sums are evaluated as
+ * sum_x F^l_a(x) F^0_b(x) F^0_c(x) over real-space filtered fields
+ * F^l_a(x) = sum_{n in a} w_l(mu) delta(n) e^{i k.x} produced by inverse
+ * 3-D FFTs ("reduced to ... products of FFTs", Sec. 3.1).
+ *
+ * Conventions.
+ *   - Grid: n^3, C order (x, y, z); z (the last axis) is the line of sight.
+ *     Index j along an axis is frequency j for j < n/2, j - n otherwise.
+ *   - delta(k) is the continuum-normalised half spectrum
+ *     delta(k) = (V/n^3) sum_x delta_x e^{-i k.x}, complex64 [n][n][n/2+1],
+ *     interleaved (re, im) float pairs.  On the n_z = 0 and n_z = n/2 planes
+ *     only the Hermitian part is used (as a real inverse FFT does).
+ *   - Shell a holds modes with edges[a]^2 <= |n|^2 < edges[a+1]^2, edges in
+ *     units of k_f = 2 pi / L, ascending.
+ *   - Bins: (a, b, c) with a >= b >= c, lexicographic, holding >= 1 triangle.
+ *
+ * Memory and ownership.
+ *   - The caller owns every device buffer passed in (inputs, outputs and the
+ *     workspace); sizes come from bsp_workspace_size.  Device pointers must
+ *     be 256-byte aligned.
+ *   - The plan owns small device tables (shell lookup, tile lists, counts)
+ *     that it allocates at creation / bsp_counts and frees on destroy.
+ *   - All GPU work is enqueued on the caller's stream (a cudaStream_t passed
+ *     as void*; NULL = legacy default stream).  bsp_counts and
+ *     bsp_compute_host synchronise that stream; bsp_compute does not.
+ *
+ * Errors.  Every entry point returns a bsp_status.  Argument errors are
+ * detected before anything is enqueued and leave the plan unchanged.
+ * CUDA errors map to BSP_ECUDA (the CUDA error string is available from
+ * bsp_last_error).  No entry point aborts, traps or exits.
+ */
+#ifndef BSP_H
+#define BSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BSP_OK = 0,
+    BSP_EINVAL = -1,        /* bad argument (null, size, order, alignment) */
+    BSP_ENOMEM = -2,        /* a plan-owned allocation failed */
+    BSP_ECUDA = -3,         /* a CUDA call or launch failed */
+    BSP_EUNSUPPORTED = -4,  /* valid request this build does not support */
+    BSP_ETIMEOUT = -5,      /* a bounded device wait gave up */
+    BSP_ESTATE = -6         /* call out of order (e.g. compute before counts) */
+} bsp_status;
+
+/* Arithmetic of the contraction (the x-sum).  Fields, counts, reductions and
+ * normalisation are FP32/FP64 whatever the choice. */
+typedef enum {
+    BSP_FP32 = 0,        /* CUDA-core FP32 FMA, FP32 partials flushed to FP64 */
+    BSP_SPLIT_BF16 = 1,  /* tcgen05 BF16 hi+lo split products, FP32 accumulate */
+    BSP_BF16 = 2         /* tcgen05 BF16 hi only (reported, not gated) */
+} bsp_precision;
+
+typedef struct bsp_plan bsp_plan;
+
+/*
+ * Create a plan for the standard estimator (Sec. 3.1).
+ *   n        grid side, even, 8 <= n <= 512, of the form 2^a 3^b 5^c.
+ *   box      box side L (> 0); V = L^3.
+ *   n_shells number of shells (1..64); edges_kf has n_shells+1 ascending
+ *            values > 0 in units of k_f, the last <= sqrt(3) n / 2.
+ *   n_ell    1..3 entries of ells, each in {0, 2, 4}, strictly ascending
+ *            (odd l vanish by parity, Sec. 3.5).
+ *   prec     a bsp_precision.
+ *   flags    0 (reserved).
+ * Host-only: allocates the plan's small device tables on the current device.
+ */
+bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells,
+                           const double* edges_kf, int n_ell, const int* ells,
+                           int prec, unsigned flags);
+
+/* Release the plan and its device tables (NULL is ignored). */
+void bsp_plan_destroy(bsp_plan* plan);
+
+/* Bytes of device workspace bsp_counts / bsp_compute need (the maximum of
+ * both).  The workspace holds the filtered fields, FFT intermediates and
+ * per-block partial sums; its contents need not persist between calls. */
+bsp_status bsp_workspace_size(const bsp_plan* plan, size_t* bytes);
+
+/*
+ * Triangle counts N_abc (V_B of Sec. 3.1, "similarly evaluated" through unit
+ * fields I_a(x) = sum_{n in a} e^{ik.x}, N_abc = n^-3 sum_x I_a I_b I_c),
+ * computed in FP64 on the GPU and rounded to integers; geometry only, so
+ * one call per plan.  Decides the valid bins (N_abc >= 1) and caches the
+ * counts and the contraction schedule in the plan.  Synchronises `stream`.
+ *   ws   device workspace of bsp_workspace_size bytes.
+ */
+bsp_status bsp_counts(bsp_plan* plan, void* ws, void* stream);
+
+/*
+ * The valid bins after bsp_counts: *n_bins always; if abc != NULL the
+ * bins as int32 [n_bins][3] (a, b, c); if counts != NULL the FP64 counts
+ * [n_bins].  BSP_ESTATE before bsp_counts.
+ */
+bsp_status bsp_plan_bins(const bsp_plan* plan, int* n_bins, int32_t* abc, double* counts);
+
+/*
+ * B^l for every valid bin (Eq. Standard_ell_Estim): enqueue filter ->
+ * inverse FFTs -> contraction -> FP64 reduction and normalisation.
+ *   delta_k  device, complex64 [n][n][n/2+1] (read only).
+ *   nbar     mean number density for Poisson shot-noise subtraction, or
+ *            0 for none (BSP_EUNSUPPORTED if > 0 in this build).
+ *   ws       device workspace of bsp_workspace_size bytes.
+ *   B        device FP64 [n_ell][n_bins], written.
+ * Asynchronous on `stream`; BSP_ESTATE before bsp_counts.
+ */
+bsp_status bsp_compute(bsp_plan* plan, const void* delta_k, double nbar, void* ws,
+                       void* stream, double* B);
+
+/*
+ * Same as bsp_compute with host buffers: copies delta_k (host, complex64
+ * [n][n][n/2+1]) to a device staging area inside ws, computes, and copies
+ * B back to host FP64 [n_ell][n_bins].  Synchronises `stream`.
+ * The workspace must be bsp_workspace_size + bsp_host_staging_size bytes.
+ */
+bsp_status bsp_compute_host(bsp_plan* plan, const void* delta_k_host, double nbar, void* ws,
+                            void* stream, double* B_host);
+bsp_status bsp_host_staging_size(const bsp_plan* plan, size_t* bytes);
+
+/* Raw sums T^l = sum_x F^l_a F_b F_c of the last bsp_compute (FP64
+ * [n_ell][n_bins], device), copied into T (device).  For tests. */
+bsp_status bsp_last_raw(const bsp_plan* plan, void* ws, void* stream, double* T);
+
+/* Human-readable text for a status, and the last CUDA error text seen by
+ * this thread ("" if none). */
+const char* bsp_status_string(int status);
+const char* bsp_last_error(void);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int bsp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSP_H */

@@ -1,0 +1,199 @@
+"""ctypes binding of libbsp (include/bsp.h): argument marshalling only.
+
+Every step of the estimator runs in the library's CUDA kernels; this module
+converts torch tensors to pointers and status codes to exceptions.  If the
+library is missing the import fails loudly -- there is no CPU fallback.
+
+The functions keep the C names (``bsp_plan_create`` ...).  ``Bispectrum`` is
+a convenience owner of a plan and its workspace.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbsp.so")
+
+BSP_OK, BSP_EINVAL, BSP_ENOMEM, BSP_ECUDA, BSP_EUNSUPPORTED, BSP_ETIMEOUT, BSP_ESTATE = 0, -1, -2, -3, -4, -5, -6
+BSP_FP32, BSP_SPLIT_BF16, BSP_BF16 = 0, 1, 2
+PRECISIONS = {"fp32": BSP_FP32, "split_bf16": BSP_SPLIT_BF16, "bf16": BSP_BF16}
+
+# (name, restype, argtypes) of every exported entry point declared in include/bsp.h
+_P = ctypes.c_void_p
+_SIGS = [
+    ("bsp_plan_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_uint]),
+    ("bsp_plan_destroy", None, [_P]),
+    ("bsp_workspace_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    ("bsp_host_staging_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    ("bsp_counts", ctypes.c_int, [_P, _P, _P]),
+    ("bsp_plan_bins", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P, _P]),
+    ("bsp_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
+    ("bsp_compute_host", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
+    ("bsp_last_raw", ctypes.c_int, [_P, _P, _P, _P]),
+    ("bsp_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("bsp_last_error", ctypes.c_char_p, []),
+    ("bsp_version", ctypes.c_int, []),
+]
+EXPORTS = [s[0] for s in _SIGS]
+
+_lib = None
+
+
+class BspError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        msg = lib.bsp_status_string(status).decode()
+        detail = lib.bsp_last_error().decode()
+        super().__init__("%s: %s (%d)%s" % (where, msg, status, (" -- " + detail) if detail else ""))
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libbsp.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise OSError("libbsp.so not built at %s (run paper_1708_05303_gb300.build.build())" % p)
+        lib = ctypes.CDLL(p)
+        for name, res, args in _SIGS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != BSP_OK:
+        raise BspError(status, where)
+
+
+def _dptr(t) -> int:
+    """Device pointer of a CUDA torch tensor (or an int)."""
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def bsp_plan_create(n: int, box: float, edges, ells=(0, 2, 4), prec: int = BSP_FP32, flags: int = 0) -> int:
+    lib = load()
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    l_ = np.ascontiguousarray(ells, dtype=np.int32)
+    h = _P()
+    st = lib.bsp_plan_create(ctypes.byref(h), int(n), float(box), int(e.size - 1),
+                             e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(l_.size),
+                             l_.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(prec), int(flags))
+    _check(st, "bsp_plan_create")
+    return h.value
+
+
+def bsp_plan_destroy(plan: int):
+    load().bsp_plan_destroy(plan)
+
+
+def bsp_workspace_size(plan: int) -> int:
+    v = ctypes.c_size_t()
+    _check(load().bsp_workspace_size(plan, ctypes.byref(v)), "bsp_workspace_size")
+    return v.value
+
+
+def bsp_host_staging_size(plan: int) -> int:
+    v = ctypes.c_size_t()
+    _check(load().bsp_host_staging_size(plan, ctypes.byref(v)), "bsp_host_staging_size")
+    return v.value
+
+
+def bsp_counts(plan: int, ws, stream=None):
+    _check(load().bsp_counts(plan, _dptr(ws), _stream_handle(stream)), "bsp_counts")
+
+
+def bsp_plan_bins(plan: int):
+    lib = load()
+    nb = ctypes.c_int()
+    _check(lib.bsp_plan_bins(plan, ctypes.byref(nb), None, None), "bsp_plan_bins")
+    abc = np.zeros((nb.value, 3), dtype=np.int32)
+    cnt = np.zeros(nb.value, dtype=np.float64)
+    _check(lib.bsp_plan_bins(plan, ctypes.byref(nb), abc.ctypes.data, cnt.ctypes.data), "bsp_plan_bins")
+    return abc, cnt
+
+
+def bsp_compute(plan: int, delta_k, B, ws, nbar: float = 0.0, stream=None):
+    _check(load().bsp_compute(plan, _dptr(delta_k), float(nbar), _dptr(ws), _stream_handle(stream), _dptr(B)),
+           "bsp_compute")
+
+
+def bsp_compute_host(plan: int, delta_k_host: np.ndarray, B_host: np.ndarray, ws, nbar: float = 0.0,
+                     stream=None):
+    """delta_k_host / B_host: numpy arrays (ideally in pinned memory) or host pointers."""
+    dptr = delta_k_host if isinstance(delta_k_host, int) else delta_k_host.ctypes.data
+    bptr = B_host if isinstance(B_host, int) else B_host.ctypes.data
+    _check(load().bsp_compute_host(plan, dptr, float(nbar), _dptr(ws), _stream_handle(stream), bptr),
+           "bsp_compute_host")
+
+
+def bsp_last_raw(plan: int, ws, T, stream=None):
+    _check(load().bsp_last_raw(plan, _dptr(ws), _stream_handle(stream), _dptr(T)), "bsp_last_raw")
+
+
+def bsp_version() -> int:
+    return int(load().bsp_version())
+
+
+class Bispectrum:
+    """A plan plus its device workspace (PyTorch-allocated), counts done on
+    construction.  ``compute(delta_k)`` returns B [n_ell][n_bins] (FP64,
+    device) for a complex64 [n][n][n/2+1] CUDA tensor."""
+
+    def __init__(self, n, box, edges, ells=(0, 2, 4), prec="fp32", host_staging=False, stream=None):
+        import torch
+
+        self.n, self.box, self.ells = int(n), float(box), tuple(ells)
+        self.plan = bsp_plan_create(n, box, edges, ells, PRECISIONS.get(prec, prec))
+        nbytes = bsp_workspace_size(self.plan)
+        if host_staging:
+            nbytes += bsp_host_staging_size(self.plan)
+        self.ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+        bsp_counts(self.plan, self.ws, stream)
+        self.bins, self.counts = bsp_plan_bins(self.plan)
+        self.B = torch.empty((len(self.ells), len(self.bins)), dtype=torch.float64, device="cuda")
+
+    def compute(self, delta_k, nbar: float = 0.0, stream=None):
+        bsp_compute(self.plan, delta_k, self.B, self.ws, nbar, stream)
+        return self.B
+
+    def compute_host(self, delta_k_host, B_host, nbar: float = 0.0, stream=None):
+        bsp_compute_host(self.plan, delta_k_host, B_host, self.ws, nbar, stream)
+        return B_host
+
+    def raw(self, stream=None):
+        import torch
+
+        T = torch.empty_like(self.B)
+        bsp_last_raw(self.plan, self.ws, T, stream)
+        return T
+
+    def close(self):
+        if getattr(self, "plan", None):
+            bsp_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,539 @@
+// bsp_api.cu -- the C ABI of libbsp (include/bsp.h): plan creation, argument
+// checks, workspace layout, scheduling of the contraction tiles, and the
+// host orchestration of filter -> inverse FFT -> contraction -> reduction.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bsp.h"
+#include "bsp_internal.h"
+
+using namespace bsp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bsp_status cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return BSP_ECUDA;
+}
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Radix stages for an inverse DFT of length m (8s first, then 4, 2, 3, 5).
+bool radix_plan(int m, int* rad, int* nrad) {
+    int a = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    std::vector<int> r;
+    int n8 = a / 3, rem = a % 3;
+    if (rem == 1 && n8 > 0) { --n8; r.push_back(4); r.push_back(4); }
+    else if (rem == 1) r.push_back(2);
+    else if (rem == 2) r.push_back(4);
+    for (int i = 0; i < n8; ++i) r.insert(r.begin(), 8);
+    while (m % 3 == 0) { m /= 3; r.push_back(3); }
+    while (m % 5 == 0) { m /= 5; r.push_back(5); }
+    if (m != 1 || (int)r.size() > 8) return false;
+    *nrad = (int)r.size();
+    for (size_t i = 0; i < r.size(); ++i) rad[i] = r[i];
+    return true;
+}
+
+struct DevSched {
+    Work* works = nullptr;
+    int2* pairs = nullptr;
+    int* rowf = nullptr;
+    BinLoc* loc = nullptr;
+    int nwork = 0, npair = 0, nrowf = 0, nloc = 0, nsplit = 1;
+    void release() {
+        cudaFree(works); cudaFree(pairs); cudaFree(rowf); cudaFree(loc);
+        works = nullptr; pairs = nullptr; rowf = nullptr; loc = nullptr;
+    }
+};
+
+struct HostSched {
+    std::vector<Work> works;
+    std::vector<int2> pairs;
+    std::vector<int> rowf;
+    std::vector<BinLoc> loc;   // [nslots_out][nbins]
+    int nsplit = 1;
+};
+
+typedef std::vector<std::array<int, 3>> BinList;
+
+// Tiles of <= 128 pairs (b, c) (sorted by b, then c; the shells they touch
+// span <= 64), each with the rows (slot, a) for a in the tile's a-range, cut
+// into chunks of <= 64 rows.
+HostSched build_sched(const BinList& bins, const std::vector<int>& out_slots, int nsh, size_t npts,
+                      int target_ctas) {
+    HostSched h;
+    std::map<std::pair<int, int>, int> pidx;
+    for (auto& t : bins) pidx[{t[1], t[2]}] = 0;
+    std::vector<std::pair<int, int>> pl;
+    for (auto& kv : pidx) pl.push_back(kv.first);   // sorted by (b, c)
+    // per pair: a-range
+    std::vector<int> alo(pl.size(), 1 << 30), ahi(pl.size(), -1);
+    for (size_t i = 0; i < pl.size(); ++i) pidx[pl[i]] = (int)i;
+    for (auto& t : bins) {
+        int p = pidx[{t[1], t[2]}];
+        alo[p] = std::min(alo[p], t[0]);
+        ahi[p] = std::max(ahi[p], t[0]);
+    }
+    struct TileInfo { int p0, np, alo, ahi, rowbase_chunk0, work0; };
+    std::vector<TileInfo> tiles;
+    size_t i = 0;
+    while (i < pl.size()) {
+        int p0 = (int)i, slo = pl[i].second, shi = pl[i].first, lo = alo[i], hi = ahi[i];
+        size_t j = i + 1;
+        while (j < pl.size() && (int)(j - i) < 128) {
+            int nslo = std::min(slo, pl[j].second), nshi = std::max(shi, pl[j].first);
+            if (nshi - nslo + 1 > 64) break;
+            slo = nslo; shi = nshi;
+            lo = std::min(lo, alo[j]); hi = std::max(hi, ahi[j]);
+            ++j;
+        }
+        TileInfo ti{p0, (int)(j - i), lo, hi, 0, (int)h.works.size()};
+        int na = hi - lo + 1, nrows = na * (int)out_slots.size();
+        for (int r0 = 0; r0 < nrows; r0 += 64) {
+            Work w{};
+            w.pair0 = p0; w.npairs = (int)(j - i);
+            w.row0 = r0; w.nrows = std::min(64, nrows - r0);
+            w.rowbase = (int)h.rowf.size();
+            w.shell_lo = slo; w.nshell = shi - slo + 1;
+            for (int r = r0; r < r0 + w.nrows; ++r) {
+                int si = r / na, a = lo + r % na;
+                h.rowf.push_back(out_slots[si] * nsh + a);
+            }
+            h.works.push_back(w);
+        }
+        tiles.push_back(ti);
+        i = j;
+    }
+    for (auto& p : pl) h.pairs.push_back(int2{p.first, p.second});
+    // pair -> tile
+    std::vector<int> tile_of(pl.size());
+    for (size_t t = 0; t < tiles.size(); ++t)
+        for (int p = tiles[t].p0; p < tiles[t].p0 + tiles[t].np; ++p) tile_of[p] = (int)t;
+    h.loc.resize(out_slots.size() * bins.size());
+    for (size_t si = 0; si < out_slots.size(); ++si)
+        for (size_t b = 0; b < bins.size(); ++b) {
+            int p = pidx[{bins[b][1], bins[b][2]}];
+            const TileInfo& ti = tiles[tile_of[p]];
+            int na = ti.ahi - ti.alo + 1;
+            int row = (int)si * na + (bins[b][0] - ti.alo);
+            BinLoc L{ti.work0 + row / 64, row % 64, p - ti.p0, 0};
+            h.loc[si * bins.size() + b] = L;
+        }
+    int nw = std::max<int>(1, (int)h.works.size());
+    long long by_len = (long long)((npts + 8191) / 8192);
+    long long by_ctas = (target_ctas + nw - 1) / nw;
+    h.nsplit = (int)std::max<long long>(1, std::min(by_len, by_ctas));
+    return h;
+}
+
+template <typename T>
+bsp_status upload(T** dst, const std::vector<T>& v) {
+    *dst = nullptr;
+    if (v.empty()) return BSP_OK;
+    CK(cudaMalloc((void**)dst, sizeof(T) * v.size()));
+    CK(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return BSP_OK;
+}
+
+bsp_status upload_sched(DevSched& d, const HostSched& h) {
+    d.release();
+    bsp_status s;
+    if ((s = upload(&d.works, h.works)) != BSP_OK) return s;
+    if ((s = upload(&d.pairs, h.pairs)) != BSP_OK) return s;
+    if ((s = upload(&d.rowf, h.rowf)) != BSP_OK) return s;
+    if ((s = upload(&d.loc, h.loc)) != BSP_OK) return s;
+    d.nwork = (int)h.works.size();
+    d.npair = (int)h.pairs.size();
+    d.nrowf = (int)h.rowf.size();
+    d.nloc = (int)h.loc.size();
+    d.nsplit = h.nsplit;
+    return BSP_OK;
+}
+
+size_t partial_bytes(const HostSched& h) {
+    return (size_t)h.works.size() * h.nsplit * 64 * 128 * sizeof(double);
+}
+
+}  // namespace
+
+struct bsp_plan {
+    int n = 0;
+    double box = 0;
+    int nsh = 0;
+    std::vector<double> edges;
+    std::vector<int> ells;       // output multipoles
+    std::vector<int> slot_ell;   // field slots: slot 0 is l = 0
+    std::vector<int> out_slots;  // slot of each output multipole
+    int prec = 0;
+    FftGeom geom{};
+    int target_ctas = 2048;
+    int16_t* d_shell_of = nullptr;
+    cx<float>* d_tw32 = nullptr;
+    cx<double>* d_tw64 = nullptr;
+    FieldDesc* d_fd_delta = nullptr;  // [nslot*nsh]
+    FieldDesc* d_fd_unit = nullptr;   // [nsh]
+    // candidate bins (superset of the valid ones) and their counting schedule
+    BinList cand;
+    HostSched cand_sched;
+    DevSched cand_dev;
+    // valid bins after counts
+    bool have_counts = false;
+    BinList bins;
+    std::vector<double> counts;
+    double* d_counts = nullptr;
+    HostSched comp_sched;
+    DevSched comp_dev;
+    // workspace layout
+    size_t fld32_bytes = 0, fld64_bytes = 0, t12_bytes32 = 0, t12_bytes64 = 0;
+    int fb32 = 1, fb64 = 1;
+    size_t part_bytes = 0, tout_bytes = 0, cnt_out_bytes = 0;
+    size_t ws_bytes = 0, staging_bytes = 0;
+
+    ~bsp_plan() {
+        cudaFree(d_shell_of); cudaFree(d_tw32); cudaFree(d_tw64);
+        cudaFree(d_fd_delta); cudaFree(d_fd_unit); cudaFree(d_counts);
+        cand_dev.release(); comp_dev.release();
+    }
+    size_t npts() const { return (size_t)n * n * n; }
+    int nslot() const { return (int)slot_ell.size(); }
+};
+
+namespace {
+
+void t12_sizes(const FftGeom& g, size_t elem, size_t* t1, size_t* t2) {
+    *t1 = round256((size_t)g.nK * g.n * g.nKz * 2 * elem);
+    *t2 = round256((size_t)g.n * g.n * g.nKz * 2 * elem);
+}
+
+// Offsets inside the workspace (the same for counts and compute; the two
+// phases reuse the same bytes).
+struct Layout {
+    size_t fields, t1, t2, partial, tout, cnt, end;
+};
+
+Layout layout_compute(const bsp_plan* p) {
+    Layout L{};
+    size_t t1, t2;
+    t12_sizes(p->geom, sizeof(float), &t1, &t2);
+    L.fields = 0;
+    L.t1 = L.fields + p->fld32_bytes;
+    L.t2 = L.t1 + t1 * p->fb32;
+    L.partial = L.t2 + t2 * p->fb32;
+    L.tout = L.partial + p->part_bytes;
+    L.cnt = L.tout + p->tout_bytes;
+    L.end = L.cnt;
+    return L;
+}
+
+Layout layout_counts(const bsp_plan* p) {
+    Layout L{};
+    size_t t1, t2;
+    t12_sizes(p->geom, sizeof(double), &t1, &t2);
+    L.fields = 0;
+    L.t1 = L.fields + p->fld64_bytes;
+    L.t2 = L.t1 + t1 * p->fb64;
+    L.partial = L.t2 + t2 * p->fb64;
+    L.tout = L.partial + round256(partial_bytes(p->cand_sched));
+    L.cnt = L.tout;
+    L.end = L.cnt + p->cnt_out_bytes;
+    return L;
+}
+
+bool good_size(int n) {
+    if (n < 8 || n > 512 || n % 2) return false;
+    int m = n;
+    for (int q : {2, 3, 5})
+        while (m % q == 0) m /= q;
+    return m == 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bsp_status_string(int s) {
+    switch (s) {
+        case BSP_OK: return "ok";
+        case BSP_EINVAL: return "invalid argument";
+        case BSP_ENOMEM: return "out of memory";
+        case BSP_ECUDA: return "CUDA error";
+        case BSP_EUNSUPPORTED: return "unsupported";
+        case BSP_ETIMEOUT: return "device wait timed out";
+        case BSP_ESTATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* bsp_last_error(void) { return g_last_error.c_str(); }
+
+int bsp_version(void) { return 100; }
+
+bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, const double* edges_kf,
+                           int n_ell, const int* ells, int prec, unsigned flags) {
+    if (!out) return BSP_EINVAL;
+    *out = nullptr;
+    if (!good_size(n) || !(box > 0) || !std::isfinite(box) || n_shells < 1 || n_shells > 64 || !edges_kf ||
+        n_ell < 1 || n_ell > 3 || !ells || flags != 0)
+        return BSP_EINVAL;
+    for (int i = 0; i <= n_shells; ++i)
+        if (!(edges_kf[i] > 0) || !std::isfinite(edges_kf[i]) || (i && !(edges_kf[i] > edges_kf[i - 1])))
+            return BSP_EINVAL;
+    if (edges_kf[n_shells] > std::sqrt(3.0) * n / 2 + 1e-9) return BSP_EINVAL;
+    for (int i = 0; i < n_ell; ++i) {
+        if (ells[i] != 0 && ells[i] != 2 && ells[i] != 4) return BSP_EINVAL;
+        if (i && ells[i] <= ells[i - 1]) return BSP_EINVAL;
+    }
+    if (prec != BSP_FP32) return BSP_EUNSUPPORTED;
+
+    bsp_plan* p = new (std::nothrow) bsp_plan();
+    if (!p) return BSP_ENOMEM;
+    p->n = n;
+    p->box = box;
+    p->nsh = n_shells;
+    p->edges.assign(edges_kf, edges_kf + n_shells + 1);
+    p->ells.assign(ells, ells + n_ell);
+    p->prec = prec;
+    p->slot_ell.push_back(0);
+    for (int l : p->ells)
+        if (l != 0) p->slot_ell.push_back(l);
+    for (int l : p->ells)
+        for (int s = 0; s < p->nslot(); ++s)
+            if (p->slot_ell[s] == l) p->out_slots.push_back(s);
+
+    // geometry and pruning
+    FftGeom& g = p->geom;
+    g.n = n;
+    const double emax = p->edges.back();
+    int K = 0;
+    while ((double)(K + 1) * (K + 1) < emax * emax) ++K;
+    if (K >= n / 2) {
+        g.K = n / 2; g.nK = n; g.pruned = 0; g.nKz = n / 2 + 1;
+    } else {
+        g.K = K; g.nK = 2 * K + 1; g.pruned = 1; g.nKz = K + 1;
+    }
+    g.n2max = 3 * (n / 2) * (n / 2);
+    if (!radix_plan(n, g.rad, &g.nrad) || !radix_plan(n / 2, g.rad_h, &g.nrad_h)) {
+        delete p;
+        return BSP_EUNSUPPORTED;
+    }
+
+    // shell lookup by integer |n|^2: lo*lo <= n2 < hi*hi
+    std::vector<int16_t> shell_of(g.n2max + 1, -1);
+    for (int n2 = 0; n2 <= g.n2max; ++n2)
+        for (int s = 0; s < n_shells; ++s) {
+            double lo = p->edges[s], hi = p->edges[s + 1];
+            if ((double)n2 >= lo * lo && (double)n2 < hi * hi) { shell_of[n2] = (int16_t)s; break; }
+        }
+    std::vector<cx<double>> tw64(n);
+    std::vector<cx<float>> tw32(n);
+    for (int t = 0; t < n; ++t) {
+        double ang = 2.0 * M_PI * (double)t / (double)n;
+        tw64[t] = {std::cos(ang), std::sin(ang)};
+        tw32[t] = {(float)tw64[t].re, (float)tw64[t].im};
+    }
+    std::vector<FieldDesc> fdd, fdu;
+    for (int s = 0; s < p->nslot(); ++s)
+        for (int a = 0; a < n_shells; ++a) fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, 0});
+    for (int a = 0; a < n_shells; ++a) fdu.push_back(FieldDesc{a, 0, FIELD_UNIT, 0});
+    bsp_status st;
+    if ((st = upload(&p->d_shell_of, shell_of)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||
+        (st = upload(&p->d_tw64, tw64)) != BSP_OK || (st = upload(&p->d_fd_delta, fdd)) != BSP_OK ||
+        (st = upload(&p->d_fd_unit, fdu)) != BSP_OK) {
+        delete p;
+        return st;
+    }
+
+    // candidate bins: every (a >= b >= c) that can hold a triangle, either
+    // without wrap-around (lo_a < hi_b + hi_c) or with it (hi_a+hi_b+hi_c > n)
+    for (int a = 0; a < n_shells; ++a)
+        for (int b = 0; b <= a; ++b)
+            for (int c = 0; c <= b; ++c) {
+                const double* e = p->edges.data();
+                if (e[a] < e[b + 1] + e[c + 1] || e[a + 1] + e[b + 1] + e[c + 1] > n)
+                    p->cand.push_back({a, b, c});
+            }
+    p->cand_sched = build_sched(p->cand, std::vector<int>{0}, n_shells, p->npts(), p->target_ctas);
+    if ((st = upload_sched(p->cand_dev, p->cand_sched)) != BSP_OK) {
+        delete p;
+        return st;
+    }
+    // workspace sizing: compute schedule bounded by the candidate bins
+    HostSched bound = build_sched(p->cand, p->out_slots, n_shells, p->npts(), p->target_ctas);
+    size_t t1, t2;
+    t12_sizes(g, sizeof(float), &t1, &t2);
+    const size_t nfields32 = (size_t)p->nslot() * n_shells;
+    p->fld32_bytes = round256(nfields32 * p->npts() * sizeof(float));
+    p->fb32 = (int)std::max<size_t>(1, std::min<size_t>(nfields32, (size_t)(2ull << 30) / (t1 + t2)));
+    t12_sizes(g, sizeof(double), &t1, &t2);
+    p->fld64_bytes = round256((size_t)n_shells * p->npts() * sizeof(double));
+    p->fb64 = (int)std::max<size_t>(1, std::min<size_t>(n_shells, (size_t)(2ull << 30) / (t1 + t2)));
+    // the valid-bin schedule has at most as many works as the bound, and
+    // nsplit <= ceil(target / nwork), so nwork * nsplit <= target + nwork
+    p->part_bytes = round256(std::max(partial_bytes(bound),
+                                      (size_t)(p->target_ctas + bound.works.size()) * 64 * 128 * sizeof(double)));
+    p->tout_bytes = round256(p->ells.size() * p->cand.size() * sizeof(double));
+    p->cnt_out_bytes = round256(p->cand.size() * sizeof(double));
+    p->ws_bytes = std::max(layout_compute(p).end, layout_counts(p).end);
+    p->staging_bytes = round256((size_t)n * n * (n / 2 + 1) * 8) + p->tout_bytes;
+    *out = p;
+    return BSP_OK;
+}
+
+void bsp_plan_destroy(bsp_plan* p) { delete p; }
+
+bsp_status bsp_workspace_size(const bsp_plan* p, size_t* bytes) {
+    if (!p || !bytes) return BSP_EINVAL;
+    *bytes = p->ws_bytes;
+    return BSP_OK;
+}
+
+bsp_status bsp_host_staging_size(const bsp_plan* p, size_t* bytes) {
+    if (!p || !bytes) return BSP_EINVAL;
+    *bytes = p->staging_bytes;
+    return BSP_OK;
+}
+
+bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
+    if (!p || !ws || !aligned256(ws)) return BSP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Layout L = layout_counts(p);
+    char* base = (char*)ws;
+    double* f64 = (double*)(base + L.fields);
+    cx<double>* t1 = (cx<double>*)(base + L.t1);
+    cx<double>* t2 = (cx<double>*)(base + L.t2);
+    size_t t1s, t2s;
+    t12_sizes(p->geom, sizeof(double), &t1s, &t2s);
+    // unit fields I_a (FP64), in batches of fb64 fields
+    for (int f0 = 0; f0 < p->nsh; f0 += p->fb64) {
+        int nf = std::min(p->fb64, p->nsh - f0);
+        cudaError_t e = launch_fft_fields<double>(p->geom, nullptr, p->d_shell_of, nullptr, p->d_fd_unit + f0, nf,
+                                                  p->d_tw64, t1, t2, f64 + (size_t)f0 * p->npts(), p->npts(), st);
+        if (e != cudaSuccess) return cuda_fail(e, "fft (counts)");
+    }
+    double* partial = (double*)(base + L.partial);
+    double* cnt = (double*)(base + L.cnt);
+    cudaError_t e = launch_contract_cc<double>(f64, p->npts(), p->cand_dev.works, p->cand_dev.nwork,
+                                               p->cand_dev.pairs, p->cand_dev.rowf, p->npts(),
+                                               p->cand_dev.nsplit, partial, st);
+    if (e != cudaSuccess) return cuda_fail(e, "contract (counts)");
+    const double n3 = (double)p->npts();
+    e = launch_reduce(partial, p->cand_dev.nsplit, p->cand_dev.loc, (int)p->cand.size(), (int)p->cand.size(),
+                      nullptr, 1.0 / n3, 0, nullptr, cnt, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce (counts)");
+    std::vector<double> hc(p->cand.size());
+    CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(double) * hc.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    p->bins.clear();
+    p->counts.clear();
+    for (size_t i = 0; i < p->cand.size(); ++i)
+        if (hc[i] >= 1.0) {
+            p->bins.push_back(p->cand[i]);
+            p->counts.push_back(hc[i]);
+        }
+    p->comp_sched = build_sched(p->bins, p->out_slots, p->nsh, p->npts(), p->target_ctas);
+    if (round256(partial_bytes(p->comp_sched)) > p->part_bytes) return BSP_ENOMEM;
+    bsp_status s = upload_sched(p->comp_dev, p->comp_sched);
+    if (s != BSP_OK) return s;
+    cudaFree(p->d_counts);
+    p->d_counts = nullptr;
+    if ((s = upload(&p->d_counts, p->counts)) != BSP_OK) return s;
+    p->have_counts = true;
+    return BSP_OK;
+}
+
+bsp_status bsp_plan_bins(const bsp_plan* p, int* n_bins, int32_t* abc, double* counts) {
+    if (!p || !n_bins) return BSP_EINVAL;
+    if (!p->have_counts) return BSP_ESTATE;
+    *n_bins = (int)p->bins.size();
+    for (size_t i = 0; i < p->bins.size(); ++i) {
+        if (abc)
+            for (int k = 0; k < 3; ++k) abc[3 * i + k] = p->bins[i][k];
+        if (counts) counts[i] = p->counts[i];
+    }
+    return BSP_OK;
+}
+
+static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, void* ws, cudaStream_t st,
+                               double* B) {
+    if (nbar != 0.0) return BSP_EUNSUPPORTED;
+    const Layout L = layout_compute(p);
+    char* base = (char*)ws;
+    float* f32 = (float*)(base + L.fields);
+    cx<float>* t1 = (cx<float>*)(base + L.t1);
+    cx<float>* t2 = (cx<float>*)(base + L.t2);
+    const int nf = p->nslot() * p->nsh;
+    for (int f0 = 0; f0 < nf; f0 += p->fb32) {
+        int nb = std::min(p->fb32, nf - f0);
+        cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, p->d_shell_of, nullptr,
+                                                 p->d_fd_delta + f0, nb, p->d_tw32, t1, t2,
+                                                 f32 + (size_t)f0 * p->npts(), p->npts(), st);
+        if (e != cudaSuccess) return cuda_fail(e, "fft");
+    }
+    double* partial = (double*)(base + L.partial);
+    double* tout = (double*)(base + L.tout);
+    cudaError_t e = launch_contract_cc<float>(f32, p->npts(), p->comp_dev.works, p->comp_dev.nwork,
+                                              p->comp_dev.pairs, p->comp_dev.rowf, p->npts(),
+                                              p->comp_dev.nsplit, partial, st);
+    if (e != cudaSuccess) return cuda_fail(e, "contract");
+    const double V = p->box * p->box * p->box;
+    e = launch_reduce(partial, p->comp_dev.nsplit, p->comp_dev.loc, p->comp_dev.nloc, (int)p->bins.size(),
+                      p->d_counts, 1.0 / (V * (double)p->npts()), 1, tout, B, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    return BSP_OK;
+}
+
+bsp_status bsp_compute(bsp_plan* p, const void* delta_k, double nbar, void* ws, void* stream, double* B) {
+    if (!p || !delta_k || !ws || !B || !aligned256(delta_k) || !aligned256(ws) || !aligned256(B) ||
+        !(nbar >= 0) || !std::isfinite(nbar))
+        return BSP_EINVAL;
+    if (!p->have_counts) return BSP_ESTATE;
+    return compute_impl(p, delta_k, nbar, ws, (cudaStream_t)stream, B);
+}
+
+bsp_status bsp_compute_host(bsp_plan* p, const void* delta_k_host, double nbar, void* ws, void* stream,
+                            double* B_host) {
+    if (!p || !delta_k_host || !ws || !B_host || !aligned256(ws) || !(nbar >= 0) || !std::isfinite(nbar))
+        return BSP_EINVAL;
+    if (!p->have_counts) return BSP_ESTATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* stage = (char*)ws + p->ws_bytes;
+    const size_t dbytes = (size_t)p->n * p->n * (p->n / 2 + 1) * 8;
+    double* Bdev = (double*)(stage + round256(dbytes));
+    CK(cudaMemcpyAsync(stage, delta_k_host, dbytes, cudaMemcpyHostToDevice, st));
+    bsp_status s = compute_impl(p, stage, nbar, ws, st, Bdev);
+    if (s != BSP_OK) return s;
+    CK(cudaMemcpyAsync(B_host, Bdev, sizeof(double) * p->ells.size() * p->bins.size(), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    return BSP_OK;
+}
+
+bsp_status bsp_last_raw(const bsp_plan* p, void* ws, void* stream, double* T) {
+    if (!p || !ws || !T || !aligned256(ws)) return BSP_EINVAL;
+    if (!p->have_counts) return BSP_ESTATE;
+    const Layout L = layout_compute(p);
+    CK(cudaMemcpyAsync(T, (char*)ws + L.tout, sizeof(double) * p->ells.size() * p->bins.size(),
+                       cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return BSP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// bsp_contract.cu -- CUDA-core contraction of filtered fields and the FP64
+// reduction / normalisation of its partial sums.
+//
+// The x-integral of Eq. Standard_ell_Estim (Sec. 3.1),
+//   T^l[a; b, c] = sum_x F^l_a(x) F^0_b(x) F^0_c(x),
+// is organised as a matrix product over x: rows r = (l, a), columns
+// p = pairs (b, c), T[r][p] = sum_x A_r(x) P_p(x) with P_p = F^0_b F^0_c formed
+// once per x and shared by every (l, a).  A work item is a tile of <= 128
+// pairs times <= 64 rows; a CTA owns one work item and one contiguous
+// x-segment, keeps 4 x 8 outputs per thread in registers, and flushes them
+// into its own FP64 partial slot every FLUSH points (the FP32 path) so that
+// FP32 accumulation never runs over more than FLUSH terms.  The reduction
+// sums the per-segment partials in a fixed order in FP64 (deterministic),
+// then normalises: B = T / (V n^3 N_abc) or N_abc = rint(T / n^3).
+#include "bsp_internal.h"
+
+namespace bsp {
+
+namespace {
+
+constexpr int CC_THREADS = 256;
+constexpr int CC_ROWS = 64;
+constexpr int CC_COLS = 128;
+
+template <typename R>
+struct CCCfg;
+template <>
+struct CCCfg<float> {
+    static constexpr int XC = 32;
+    static constexpr int FLUSH = 8192;
+};
+template <>
+struct CCCfg<double> {
+    static constexpr int XC = 16;
+    static constexpr int FLUSH = 1 << 30;
+};
+
+template <typename R, int N>
+struct Vec;
+template <>
+struct Vec<float, 4> {
+    static __device__ __forceinline__ void ld(const float* p, float* v) {
+        float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <>
+struct Vec<double, 4> {
+    static __device__ __forceinline__ void ld(const double* p, double* v) {
+        double2 t0 = reinterpret_cast<const double2*>(p)[0];
+        double2 t1 = reinterpret_cast<const double2*>(p)[1];
+        v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+    }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict__ fields, size_t fstride,
+                                                            const Work* __restrict__ works,
+                                                            const int2* __restrict__ pair_fields,
+                                                            const int* __restrict__ row_fields,
+                                                            size_t npts, size_t seg,
+                                                            double* __restrict__ partial) {
+    constexpr int XC = CCCfg<R>::XC;
+    constexpr int FLUSH = CCCfg<R>::FLUSH;
+    constexpr int AS = CC_ROWS + 4;   // padded row strides (multiples of 16 bytes)
+    constexpr int PS = CC_COLS + 4;
+    __shared__ __align__(16) R As[XC][AS];
+    __shared__ __align__(16) R Ps[XC][PS];
+    __shared__ __align__(16) R Fz[64][XC];
+    __shared__ int2 pf[CC_COLS];
+    __shared__ int rf[CC_ROWS];
+
+    const Work w = works[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ty = (warp & 1) * 8 + (lane >> 2);     // rows 4*ty .. 4*ty+3
+    const int tx = (warp >> 1) * 4 + (lane & 3);     // cols 8*tx .. 8*tx+7
+    for (int i = tid; i < CC_COLS; i += CC_THREADS) {
+        int2 v = {-1, -1};
+        if (i < w.npairs) {
+            v = pair_fields[w.pair0 + i];
+            v.x -= w.shell_lo;
+            v.y -= w.shell_lo;
+        }
+        pf[i] = v;
+    }
+    for (int i = tid; i < CC_ROWS; i += CC_THREADS) rf[i] = i < w.nrows ? row_fields[w.rowbase + i] : -1;
+
+    const size_t x_begin = (size_t)blockIdx.y * seg;
+    const size_t x_end = min(npts, x_begin + seg);
+    double* slot = partial + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (CC_ROWS * CC_COLS);
+
+    R acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = (R)0;
+    bool first = true;
+    size_t since_flush = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                double* d = slot + (size_t)(ty * 4 + i) * CC_COLS + tx * 8 + j;
+                *d = first ? (double)acc[i][j] : *d + (double)acc[i][j];
+                acc[i][j] = (R)0;
+            }
+        first = false;
+    };
+    __syncthreads();
+
+    for (size_t x0 = x_begin; x0 < x_end; x0 += XC) {
+        const int nx = (int)min((size_t)XC, x_end - x0);
+        for (int e = tid; e < w.nshell * XC; e += CC_THREADS) {
+            const int s = e / XC, x = e % XC;
+            Fz[s][x] = x < nx ? fields[(size_t)(w.shell_lo + s) * fstride + x0 + x] : (R)0;
+        }
+        for (int e = tid; e < CC_ROWS * XC; e += CC_THREADS) {
+            const int r = e / XC, x = e % XC;
+            const int f = rf[r];
+            As[x][r] = (f >= 0 && x < nx) ? fields[(size_t)f * fstride + x0 + x] : (R)0;
+        }
+        __syncthreads();
+        for (int e = tid; e < CC_COLS * XC; e += CC_THREADS) {
+            const int p = e % CC_COLS, x = e / CC_COLS;
+            const int2 bc = pf[p];
+            Ps[x][p] = bc.x >= 0 ? Fz[bc.x][x] * Fz[bc.y][x] : (R)0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int x = 0; x < XC; ++x) {
+            R a[4], p[8];
+            Vec<R, 4>::ld(&As[x][ty * 4], a);
+            Vec<R, 4>::ld(&Ps[x][tx * 8], p);
+            Vec<R, 4>::ld(&Ps[x][tx * 8 + 4], p + 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], p[j], acc[i][j]);
+        }
+        __syncthreads();
+        since_flush += XC;
+        if (since_flush >= (size_t)FLUSH) {
+            flush();
+            since_flush = 0;
+        }
+    }
+    flush();
+}
+
+__global__ void k_reduce(const double* __restrict__ partial, int nsplit, const BinLoc* __restrict__ loc,
+                         int nout, int nbins, const double* __restrict__ counts, double scale, int mode,
+                         double* __restrict__ T_out, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nout) return;
+    const BinLoc L = loc[i];
+    const double* p = partial + (size_t)L.work * nsplit * (CC_ROWS * CC_COLS) + (size_t)L.row * CC_COLS + L.col;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += p[(size_t)k * (CC_ROWS * CC_COLS)];
+    if (T_out) T_out[i] = s;
+    if (mode == 0) out[i] = rint(s * scale);
+    else out[i] = s * scale / counts[i % nbins];
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_contract_cc(const R* fields, size_t fstride, const Work* works, int nwork,
+                               const int2* pair_fields, const int* row_fields, size_t npts, int nsplit,
+                               double* partial, cudaStream_t st) {
+    constexpr int XC = CCCfg<R>::XC;
+    size_t seg = (npts + nsplit - 1) / nsplit;
+    seg = (seg + XC - 1) / XC * XC;
+    dim3 grid(nwork, nsplit);
+    k_contract_cc<R><<<grid, CC_THREADS, 0, st>>>(fields, fstride, works, pair_fields, row_fields, npts, seg,
+                                                  partial);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_contract_cc<float>(const float*, size_t, const Work*, int, const int2*, const int*,
+                                               size_t, int, double*, cudaStream_t);
+template cudaError_t launch_contract_cc<double>(const double*, size_t, const Work*, int, const int2*,
+                                                const int*, size_t, int, double*, cudaStream_t);
+
+cudaError_t launch_reduce(const double* partial, int nsplit, const BinLoc* loc, int nout, int nbins,
+                          const double* counts, double scale, int mode, double* T_out, double* out,
+                          cudaStream_t st) {
+    if (nout <= 0) return cudaSuccess;
+    k_reduce<<<(nout + 255) / 256, 256, 0, st>>>(partial, nsplit, loc, nout, nbins, counts, scale, mode, T_out,
+                                                 out);
+    return cudaGetLastError();
+}
+
+}  // namespace bsp

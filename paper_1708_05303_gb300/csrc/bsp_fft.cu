@@ -1,0 +1,342 @@
+// bsp_fft.cu -- shell/Legendre filter fused into a pruned, batched inverse
+// 3-D FFT (complex along x, complex along y, complex-to-real along z).
+//
+// Computes, for each requested field f (Sec. 3.1: the filtered real-space
+// fields D^{(l)}_k(x) = int_k d^3q e^{iq.x} delta^{(l)}(q) under
+// Eq. Standard_ell_Estim; Sec. 3.5: M^{(l)}_n(x) of Eq. betaEst),
+//
+//   F_f(x) = sum_n W_f(n) S_f(n) e^{+2 pi i n.x / N},
+//   W_f(n) = w_l(mu) x {1[n in shell] | R_p[|n|^2]},  w_l = (2l+1) L_l,
+//   S_f(n) = delta(n) | 1 | |delta(n)|^2,
+//
+// over the Hermitian half spectrum delta[N][N][N/2+1].  No 1/N^3 factor.
+//
+// Pruning: all weights vanish for |n| >= the last shell edge, so only
+// frequencies |f| <= K on x and y and 0 <= f_z < nKz are carried:
+//   pass 1: per (f_y, f_z) pencil, filter + inverse DFT along x
+//           -> T1[f_y (compact)][x][f_z]
+//   pass 2: per (x, f_z) pencil, inverse DFT along y -> T2[x][y][f_z]
+//   pass 3: per (x, y) pencil, real inverse DFT along z -> F[x][y][z]
+// Each pass stages a batch of pencils in shared memory, so global reads and
+// writes are contiguous runs; the 1-D transforms are in-place Stockham
+// autosort radix-2/3/4/5/8 stages, ping-ponging between two shared-memory
+// buffers with one barrier per stage.  Twiddles come from a host table of
+// exp(+2 pi i t/N) computed in FP64.
+#include "bsp_internal.h"
+
+namespace bsp {
+
+namespace {
+
+constexpr int NTHR = 256;
+
+template <typename R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> cmuli(cx<R> a) { return {-a.im, a.re}; }   // i * a
+template <typename R>
+__device__ __forceinline__ cx<R> cscale(cx<R> a, R s) { return {a.re * s, a.im * s}; }
+
+// Inverse (sign +1) DFT of RADIX values in registers: y_q = sum_r v_r e^{+2 pi i r q / RADIX}.
+template <typename R, int RADIX>
+__device__ __forceinline__ void butterfly(cx<R>* v) {
+    if constexpr (RADIX == 2) {
+        cx<R> a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (RADIX == 4) {
+        cx<R> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        cx<R> s13 = cadd(v[1], v[3]), d13 = cmuli(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    } else if constexpr (RADIX == 8) {
+        cx<R> e[4] = {v[0], v[2], v[4], v[6]};
+        cx<R> o[4] = {v[1], v[3], v[5], v[7]};
+        butterfly<R, 4>(e);
+        butterfly<R, 4>(o);
+        const R h = (R)0.70710678118654752440;   // 1/sqrt(2)
+        cx<R> w1o = {(o[1].re - o[1].im) * h, (o[1].re + o[1].im) * h};     // e^{i pi/4} o1
+        cx<R> w2o = cmuli(o[2]);                                             // e^{i pi/2} o2
+        cx<R> w3o = {-(o[3].re + o[3].im) * h, (o[3].re - o[3].im) * h};    // e^{3i pi/4} o3
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], w1o);
+        v[5] = csub(e[1], w1o);
+        v[2] = cadd(e[2], w2o);
+        v[6] = csub(e[2], w2o);
+        v[3] = cadd(e[3], w3o);
+        v[7] = csub(e[3], w3o);
+    } else if constexpr (RADIX == 3) {
+        const R s3 = (R)0.86602540378443864676;  // sqrt(3)/2
+        cx<R> t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        cx<R> m = {v[0].re - (R)0.5 * t.re, v[0].im - (R)0.5 * t.im};
+        cx<R> id = cmuli(cscale(d, s3));
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, id);
+        v[2] = csub(m, id);
+    } else if constexpr (RADIX == 5) {
+        const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;   // cos 2pi/5, cos 4pi/5
+        const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;    // sin 2pi/5, sin 4pi/5
+        cx<R> t1 = cadd(v[1], v[4]), d1 = csub(v[1], v[4]);
+        cx<R> t2 = cadd(v[2], v[3]), d2 = csub(v[2], v[3]);
+        cx<R> a1 = {v[0].re + c1 * t1.re + c2 * t2.re, v[0].im + c1 * t1.im + c2 * t2.im};
+        cx<R> a2 = {v[0].re + c2 * t1.re + c1 * t2.re, v[0].im + c2 * t1.im + c1 * t2.im};
+        cx<R> b1 = cmuli(cx<R>{s1 * d1.re + s2 * d2.re, s1 * d1.im + s2 * d2.im});
+        cx<R> b2 = cmuli(cx<R>{s2 * d1.re - s1 * d2.re, s2 * d1.im - s1 * d2.im});
+        v[0] = cadd(v[0], cadd(t1, t2));
+        v[1] = cadd(a1, b1);
+        v[4] = csub(a1, b1);
+        v[2] = cadd(a2, b2);
+        v[3] = csub(a2, b2);
+    }
+}
+
+// One Stockham stage of radix RADIX over P pencils of length M, out of
+// place from src to dst in shared memory; element (pencil p, index i) lives
+// at buf[p*ps + i*is].  Butterfly j reads x[j + r M/RADIX], twiddles by
+// W_M^{r (j mod Ns) M/(Ns RADIX)} and writes y[(j/Ns) Ns RADIX + j mod Ns + r Ns]
+// (autosort: natural order after the last stage).
+template <typename R, int RADIX, bool pfast>
+__device__ __forceinline__ void fft_stage(const cx<R>* __restrict__ src, cx<R>* __restrict__ dst, int M,
+                                          int Ns, int P, int ps, int is, const cx<R>* tw, int twmul) {
+    const int nbf = M / RADIX;
+    const int total = nbf * P;
+    for (int b = threadIdx.x; b < total; b += NTHR) {
+        int p, j;
+        if (pfast) { p = b % P; j = b / P; } else { j = b % nbf; p = b / nbf; }
+        const int k = j % Ns;
+        const int tstep = k * (M / (Ns * RADIX)) * twmul;
+        const cx<R>* in = src + p * ps;
+        cx<R> v[RADIX];
+#pragma unroll
+        for (int r = 0; r < RADIX; ++r) {
+            cx<R> x = in[(j + r * nbf) * is];
+            v[r] = r == 0 ? x : cmul(x, tw[r * tstep]);
+        }
+        butterfly<R, RADIX>(v);
+        cx<R>* out = dst + p * ps;
+        const int o = (j / Ns) * Ns * RADIX + k;
+#pragma unroll
+        for (int r = 0; r < RADIX; ++r) out[(o + r * Ns) * is] = v[r];
+    }
+    __syncthreads();
+}
+
+// Inverse DFT of P pencils held in a; b is scratch of the same shape.
+// Returns the buffer that holds the result.
+template <typename R, bool pfast>
+__device__ cx<R>* fft_pingpong(cx<R>* a, cx<R>* b, int M, int P, int ps, int is, const int* rad, int nrad,
+                               const cx<R>* tw, int twmul) {
+    int Ns = 1;
+    for (int s = 0; s < nrad; ++s) {
+        switch (rad[s]) {
+            case 8: fft_stage<R, 8, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
+            case 4: fft_stage<R, 4, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
+            case 2: fft_stage<R, 2, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
+            case 3: fft_stage<R, 3, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
+            case 5: fft_stage<R, 5, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
+        }
+        Ns *= rad[s];
+        cx<R>* t = a; a = b; b = t;
+    }
+    return a;
+}
+
+__device__ __forceinline__ int freq_of(int idx, int n) { return idx < n / 2 ? idx : idx - n; }
+
+// W_f(n): the field's radial factor times w_l(mu), mu^2 = n_z^2/|n|^2.
+template <typename R>
+__device__ __forceinline__ R filter_weight(const FieldDesc& fd, int n2, int fz, const int16_t* shell_of,
+                                           const float* radial, int n2max) {
+    if (n2 <= 0 || n2 > n2max) return (R)0;
+    R base;
+    if (fd.kind == FIELD_RADIAL) base = (R)radial[(size_t)fd.shell * (n2max + 1) + n2];
+    else base = (shell_of[n2] == fd.shell) ? (R)1 : (R)0;
+    if (base == (R)0 || fd.ell == 0) return base;
+    const R mu2 = (R)(fz * fz) / (R)n2;
+    if (fd.ell == 2) return base * (R)2.5 * ((R)3 * mu2 - (R)1);                       // 5 L_2
+    return base * (R)1.125 * (((R)35 * mu2 - (R)30) * mu2 + (R)3);                     // 9 L_4
+}
+
+// Pass 1: filter + inverse DFT along x for P consecutive f_z of one f_y.
+template <typename R, int P>
+__global__ void __launch_bounds__(NTHR) k_pass1(FftGeom g, const cx<float>* __restrict__ delta,
+                                                const int16_t* __restrict__ shell_of,
+                                                const float* __restrict__ radial,
+                                                const FieldDesc* __restrict__ fields,
+                                                const cx<R>* __restrict__ twg, cx<R>* __restrict__ t1,
+                                                size_t t1_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
+    cx<R>* buf = tw + g.n;
+    cx<R>* scr = buf + g.n * P;
+    const int N = g.n;
+    const FieldDesc fd = fields[blockIdx.y];
+    const int nkzb = (g.nKz + P - 1) / P;
+    const int cy = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P;
+    const int fy = g.pruned ? cy - g.K : freq_of(cy, N);
+    const int iy = (fy + N) % N;
+    for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
+    for (int e = threadIdx.x; e < N * P; e += NTHR) {
+        const int p = e % P, ix = e / P, kz = kz0 + p;
+        const int fx = freq_of(ix, N);
+        cx<R> val = {(R)0, (R)0};
+        if (kz < g.nKz && (!g.pruned || (fx >= -g.K && fx <= g.K))) {
+            const int fz = (kz == N / 2) ? -(N / 2) : kz;
+            const int n2 = fx * fx + fy * fy + fz * fz;
+            const R w = filter_weight<R>(fd, n2, fz, shell_of, radial, g.n2max);
+            if (w != (R)0) {
+                if (fd.kind == FIELD_UNIT) {
+                    val.re = w;
+                } else {
+                    const cx<float> d = delta[((size_t)ix * N + iy) * (N / 2 + 1) + kz];
+                    if (fd.kind == FIELD_POWER) {
+                        val.re = w * ((R)d.re * (R)d.re + (R)d.im * (R)d.im);
+                    } else {
+                        val.re = w * (R)d.re;
+                        val.im = w * (R)d.im;
+                    }
+                }
+            }
+        }
+        buf[ix * P + p] = val;
+    }
+    __syncthreads();
+    const cx<R>* res = fft_pingpong<R, true>(buf, scr, N, P, 1, P, g.rad, g.nrad, tw, 1);
+    cx<R>* dst = t1 + (size_t)blockIdx.y * t1_stride;
+    for (int e = threadIdx.x; e < N * P; e += NTHR) {
+        const int p = e % P, x = e / P, kz = kz0 + p;
+        if (kz < g.nKz) dst[((size_t)cy * N + x) * g.nKz + kz] = res[x * P + p];
+    }
+}
+
+// Pass 2: inverse DFT along y for P consecutive f_z of one x.
+template <typename R, int P>
+__global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restrict__ t1,
+                                                size_t t1_stride, const cx<R>* __restrict__ twg,
+                                                cx<R>* __restrict__ t2, size_t t2_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
+    cx<R>* buf = tw + g.n;
+    cx<R>* scr = buf + g.n * P;
+    const int N = g.n;
+    const int nkzb = (g.nKz + P - 1) / P;
+    const int x = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P;
+    const cx<R>* src = t1 + (size_t)blockIdx.y * t1_stride;
+    for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
+    for (int e = threadIdx.x; e < N * P; e += NTHR) {
+        const int p = e % P, iy = e / P, kz = kz0 + p;
+        const int fy = freq_of(iy, N);
+        cx<R> val = {(R)0, (R)0};
+        if (kz < g.nKz && (!g.pruned || (fy >= -g.K && fy <= g.K))) {
+            const int cy = g.pruned ? fy + g.K : iy;
+            val = src[((size_t)cy * N + x) * g.nKz + kz];
+        }
+        buf[iy * P + p] = val;
+    }
+    __syncthreads();
+    const cx<R>* res = fft_pingpong<R, true>(buf, scr, N, P, 1, P, g.rad, g.nrad, tw, 1);
+    cx<R>* dst = t2 + (size_t)blockIdx.y * t2_stride;
+    for (int e = threadIdx.x; e < N * P; e += NTHR) {
+        const int p = e % P, y = e / P, kz = kz0 + p;
+        if (kz < g.nKz) dst[((size_t)x * N + y) * g.nKz + kz] = res[y * P + p];
+    }
+}
+
+// Pass 3: real inverse DFT along z for P consecutive y of one x, through a
+// complex DFT of length M = N/2:  Z_k = (H_k + conj H_{M-k})
+//   + i (H_k - conj H_{M-k}) e^{2 pi i k/N},  F[2m] = Re z_m, F[2m+1] = Im z_m,
+// with Im H_0 = Im H_M = 0 (the Hermitian part of the n_z = 0, N/2 planes).
+template <typename R, int P>
+__global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restrict__ t2,
+                                                size_t t2_stride, const cx<R>* __restrict__ twg,
+                                                R* __restrict__ out, size_t out_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
+    cx<R>* buf = tw + g.n;
+    const int N = g.n, M = N / 2, ps = M + 1;
+    cx<R>* scr = buf + P * ps;
+    const int nyb = (N + P - 1) / P;
+    const int x = blockIdx.x / nyb, y0 = (blockIdx.x % nyb) * P;
+    const cx<R>* src = t2 + (size_t)blockIdx.y * t2_stride;
+    for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
+    __syncthreads();
+    for (int e = threadIdx.x; e < M * P; e += NTHR) {
+        const int k = e % M, p = e / M, y = y0 + p;
+        cx<R> z = {(R)0, (R)0};
+        if (y < N) {
+            const cx<R>* h = src + ((size_t)x * N + y) * g.nKz;
+            cx<R> a = {(R)0, (R)0}, b = {(R)0, (R)0};
+            if (k < g.nKz) a = h[k];
+            if (M - k < g.nKz) b = h[M - k];
+            if (k == 0) { a.im = (R)0; b.im = (R)0; }   // H_0 and H_M: real parts only
+            const cx<R> bc = {b.re, -b.im};
+            const cx<R> s = cadd(a, bc), d = csub(a, bc);
+            z = cadd(s, cmuli(cmul(d, tw[k])));
+        }
+        buf[p * ps + k] = z;
+    }
+    __syncthreads();
+    const cx<R>* res = fft_pingpong<R, false>(buf, scr, M, P, ps, 1, g.rad_h, g.nrad_h, tw, 2);
+    R* dst = out + (size_t)blockIdx.y * out_stride;
+    for (int e = threadIdx.x; e < M * P; e += NTHR) {
+        const int m = e % M, p = e / M, y = y0 + p;
+        if (y < N) reinterpret_cast<cx<R>*>(dst + ((size_t)x * N + y) * N)[m] = res[p * ps + m];
+    }
+}
+
+template <typename R>
+struct FftCfg;
+template <>
+struct FftCfg<float> {
+    static constexpr int P = 8, P3 = 16;
+};
+template <>
+struct FftCfg<double> {
+    static constexpr int P = 4, P3 = 8;
+};
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const int16_t* shell_of,
+                              const float* radial, const FieldDesc* d_fields, int nfields,
+                              const cx<R>* tw, cx<R>* t1, cx<R>* t2, R* out, size_t out_stride,
+                              cudaStream_t st) {
+    using C = FftCfg<R>;
+    const int N = g.n, M = N / 2;
+    const size_t t1_stride = (size_t)g.nK * N * g.nKz;
+    const size_t t2_stride = (size_t)N * N * g.nKz;
+    const size_t sm12 = sizeof(cx<R>) * ((size_t)N + 2 * (size_t)N * C::P);
+    const size_t sm3 = sizeof(cx<R>) * ((size_t)N + 2 * (size_t)C::P3 * (M + 1));
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_pass1<R, C::P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm12)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_pass2<R, C::P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm12)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_pass3<R, C::P3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm3)) != cudaSuccess) return e;
+    const int nkzb = (g.nKz + C::P - 1) / C::P;
+    dim3 g1(g.nK * nkzb, nfields), g2(N * nkzb, nfields), g3(N * ((N + C::P3 - 1) / C::P3), nfields);
+    k_pass1<R, C::P><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);
+    k_pass2<R, C::P><<<g2, NTHR, sm12, st>>>(g, t1, t1_stride, tw, t2, t2_stride);
+    k_pass3<R, C::P3><<<g3, NTHR, sm3, st>>>(g, t2, t2_stride, tw, out, out_stride);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fft_fields<float>(const FftGeom&, const cx<float>*, const int16_t*, const float*,
+                                              const FieldDesc*, int, const cx<float>*, cx<float>*,
+                                              cx<float>*, float*, size_t, cudaStream_t);
+template cudaError_t launch_fft_fields<double>(const FftGeom&, const cx<float>*, const int16_t*, const float*,
+                                               const FieldDesc*, int, const cx<double>*, cx<double>*,
+                                               cx<double>*, double*, size_t, cudaStream_t);
+
+}  // namespace bsp

@@ -1,0 +1,83 @@
+// bsp_internal.h -- declarations shared by the libbsp translation units.
+// Not part of the public ABI (include/bsp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace bsp {
+
+template <typename R>
+struct __align__(2 * sizeof(R)) cx {
+    R re, im;
+};
+
+// What a filtered field is made of (Sec. 3.1 D_k^{(l)}, Sec. 3.5 M^{(l)}_n).
+enum FieldKind : int {
+    FIELD_DELTA = 0,    // w_l(mu) 1[n in shell] delta(n)
+    FIELD_UNIT = 1,     // w_l(mu) 1[n in shell]            (counts: delta == 1)
+    FIELD_POWER = 2,    // w_l(mu) 1[n in shell] |delta(n)|^2  (shot noise)
+    FIELD_RADIAL = 3,   // w_l(mu) R_p[n^2] delta(n)        (modal)
+};
+
+struct FieldDesc {
+    int shell;   // shell index (FIELD_DELTA/UNIT/POWER) or radial table row (FIELD_RADIAL)
+    int ell;     // 0, 2, 4
+    int kind;    // FieldKind
+    int pad;
+};
+
+// Geometry of the pruned inverse FFT.  Only frequencies |f| <= K per axis
+// can be nonzero (all filters vanish for |n| >= the last edge).
+struct FftGeom {
+    int n;        // grid side
+    int K;        // largest kept |frequency| on x, y (pruned) -- n/2 when not pruned
+    int nK;       // kept x/y frequencies: 2K+1 (pruned) or n
+    int pruned;   // 1 if nK < n
+    int nKz;      // kept z frequencies 0..nKz-1 (<= n/2+1)
+    int n2max;    // largest |n|^2 in the shell table
+    int nrad;     // radix stages for length n
+    int rad[8];
+    int nrad_h;   // radix stages for length n/2 (real-output pass)
+    int rad_h[8];
+};
+
+// One contraction work item: a tile of pairs (b, c) (contiguous indices in
+// the pair table) times a chunk of up to 64 rows (l, a).
+struct Work {
+    int pair0;    // first pair index
+    int npairs;   // <= 128
+    int row0;     // first row of the tile's (l, a) row list
+    int nrows;    // <= 64
+    int rowbase;  // index into the row-field table of row 0 of this chunk
+    int shell_lo; // lowest shell used by the pairs
+    int nshell;   // shells shell_lo .. shell_lo + nshell - 1 (<= 64)
+    int pad;
+};
+
+struct BinLoc {   // where T of (l, bin) lives in the partial buffer
+    int work;
+    int row;      // row within the work item
+    int col;      // pair within the work item
+    int pad;
+};
+
+// ---- launchers (bsp_fft.cu) ----
+template <typename R>
+cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const int16_t* shell_of,
+                              const float* radial, const FieldDesc* d_fields, int nfields,
+                              const cx<R>* tw, cx<R>* t1, cx<R>* t2, R* out, size_t out_stride,
+                              cudaStream_t st);
+
+// ---- launchers (bsp_contract.cu) ----
+template <typename R>
+cudaError_t launch_contract_cc(const R* fields, size_t fstride, const Work* works, int nwork,
+                               const int2* pair_fields, const int* row_fields, size_t npts,
+                               int nsplit, double* partial, cudaStream_t st);
+
+cudaError_t launch_reduce(const double* partial, int nsplit, const BinLoc* loc, int nout,
+                          int nbins, const double* counts, double scale, int mode, double* T_out,
+                          double* out, cudaStream_t st);
+
+}  // namespace bsp

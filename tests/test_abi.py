@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point
+declared in include/bsp.h, and rejects bad arguments before touching CUDA."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1708_05303_gb300 import build, bsp
+
+    build.build()
+    return bsp.load()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(bsp_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1708_05303_gb300 import bsp
+
+    decl = declared_symbols()
+    assert "bsp_compute" in decl and "bsp_counts" in decl
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert set(bsp.EXPORTS) == decl
+
+
+def test_version_and_strings(lib):
+    from paper_1708_05303_gb300 import bsp
+
+    assert bsp.bsp_version() >= 100
+    assert lib.bsp_status_string(-1) == b"invalid argument"
+    assert lib.bsp_status_string(0) == b"ok"
+
+
+@pytest.mark.parametrize("kwargs", [
+    dict(n=63, box=1000.0, edges=[1, 3], ells=(0,)),          # odd n
+    dict(n=14, box=1000.0, edges=[1, 3], ells=(0,)),          # 7 is not a radix
+    dict(n=64, box=-1.0, edges=[1, 3], ells=(0,)),            # box
+    dict(n=64, box=1000.0, edges=[3, 1], ells=(0,)),          # edges not ascending
+    dict(n=64, box=1000.0, edges=[0, 1], ells=(0,)),          # edge 0
+    dict(n=64, box=1000.0, edges=[1, 60], ells=(0,)),         # beyond sqrt(3) n / 2
+    dict(n=64, box=1000.0, edges=[1, 3], ells=(1,)),          # odd l
+    dict(n=64, box=1000.0, edges=[1, 3], ells=(2, 0)),        # not ascending
+    dict(n=64, box=1000.0, edges=[1, 3], ells=(0, 2, 4, 6)),  # too many / l = 6
+    dict(n=1024, box=1000.0, edges=[1, 3], ells=(0,)),        # too large for this build
+])
+def test_bad_arguments_rejected_on_host(lib, kwargs):
+    from paper_1708_05303_gb300 import bsp
+
+    with pytest.raises(bsp.BspError) as ei:
+        bsp.bsp_plan_create(kwargs["n"], kwargs["box"], kwargs["edges"], kwargs["ells"])
+    assert ei.value.status == bsp.BSP_EINVAL
+
+
+def test_null_arguments(lib):
+    import ctypes
+
+    from paper_1708_05303_gb300 import bsp
+
+    assert lib.bsp_workspace_size(None, None) == bsp.BSP_EINVAL
+    assert lib.bsp_counts(None, None, None) == bsp.BSP_EINVAL
+    assert lib.bsp_compute(None, None, 0.0, None, None, None) == bsp.BSP_EINVAL
+    n = ctypes.c_int()
+    assert lib.bsp_plan_bins(None, ctypes.byref(n), None, None) == bsp.BSP_EINVAL
+    lib.bsp_plan_destroy(None)
