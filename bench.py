@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Benchmark of the FFT bispectrum-multipole estimator (arXiv:1708.05303, Sec. 3.1).
+
+One step = one full bsp_compute on one synthetic realisation: shell/Legendre
+filter + batched inverse 3-D FFTs of every field + contraction of all valid
+bins + FP64 reduction and normalisation.  Workload: 512^3 grid, L = 1000
+Mpc/h, 64 shells of width 2 k_f from k_f, l = 0, 2, 4 (25 424 bins x 3).
+The triangle counts are geometry only; they are computed once before the
+timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+independent realisation (replicas; no collective on the data path) and the
+value is the bins all ranks finished divided by the slowest rank's time.
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample
+of the same workload, extrapolated to the whole step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "B_0,2,4 bins/s at 512^3, 64 shells; split-BF16 vs FP32 speedup at 1e-5 err"
+BOX = 1000.0
+SEED = 1708 + 2          # the 512^3 workload's seed
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--shells", type=int, default=64)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "split_bf16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n, shells):
+    from paper_1708_05303_gb300.synth import linear_edges
+
+    edges = linear_edges(shells)
+    desc = ("%d^3 grid, L=%g Mpc/h, sigma_g=0.3 quadratic+Kaiser field, %d shells of width 2 k_f from k_f, "
+            "l=0,2,4" % (n, BOX, shells))
+    return edges, desc
+
+
+def make_input(n):
+    from paper_1708_05303_gb300.synth import FieldModel, make_field
+
+    dk, _ = make_field(FieldModel(n=n, box=BOX, sigma_g=0.3), SEED)
+    return dk
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_sample(dk, n, edges, n_fields=1, n_bins=4):
+    """Time the oracle on a bounded sample of the step and extrapolate: one
+    Hermitian completion, ``n_fields`` filtered fields (own FP64 FFT) and
+    ``n_bins`` triple sums over all n^3 points; the step needs 3 x n_shells
+    fields and 3 x n_bins_valid sums (the counts are geometry, excluded on
+    both sides)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    full = oracle.full_from_half(dk.astype(np.complex128), n)
+    t_full = time.perf_counter() - t0
+    masks = oracle.shell_masks(n, edges)
+    mu = oracle.mu_grid(n)
+    ns = len(edges) - 1
+    fields = []
+    t0 = time.perf_counter()
+    for i in range(n_fields):
+        a = ns - 1 - i
+        fields.append(oracle.real_field(full, oracle.legendre_weight(2, mu) * masks[a]))
+    t_field = (time.perf_counter() - t0) / n_fields
+    while len(fields) < 3:
+        fields.append(fields[-1])
+    t0 = time.perf_counter()
+    oracle.sum3(fields, [(0, 1, 2)] * n_bins)
+    t_bin = (time.perf_counter() - t0) / n_bins
+    return dict(t_full=t_full, t_field=t_field, t_bin=t_bin, cores=oracle.num_threads(),
+                sample="%d^3: Hermitian completion + %d filtered field(s) + %d triple sums, extrapolated to "
+                       "%d fields + all bin sums" % (n, n_fields, n_bins, 3 * ns))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    edges, desc = workload(args.n, args.shells)
+    import oracle
+
+    dk = make_input(args.n)
+    cand = oracle.candidate_triplets(args.shells)
+    # valid bins of this geometry (no triangle can reach a > b + c + 2 for width-2 shells without wrap)
+    nb = sum(1 for (a, b, c) in cand if edges[a] < edges[b + 1] + edges[c + 1])
+    total_out = 3 * nb
+    times = []
+    info = None
+    for it in range(args.warmup + args.steps):
+        info = cpu_sample(dk, args.n, edges)
+        step_s = info["t_full"] + 3 * args.shells * info["t_field"] + total_out * info["t_bin"]
+        if it >= args.warmup:
+            times.append(step_s)
+    t = statistics.median(times)
+    v = total_out / t
+    line = {"metric": METRIC, "value": v, "unit": "bins/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": desc, "bins": nb, "outputs": total_out},
+            "cpu_baseline": {"kind": "oracle", "value": v, "unit": "bins/s", "cores": info["cores"],
+                             "sample": info["sample"]},
+            "e2e": {"value": v, "unit": "bins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1708_05303_gb300 import build as B
+
+    B.build()
+    from paper_1708_05303_gb300 import bsp
+
+    edges, desc = workload(args.n, args.shells)
+    dk = make_input(args.n)
+    t0 = time.perf_counter()
+    est = bsp.Bispectrum(args.n, BOX, edges, (0, 2, 4), prec=args.prec, host_staging=not args.no_e2e)
+    torch.cuda.synchronize()
+    t_counts = time.perf_counter() - t0
+    nbins = len(est.bins)
+    outputs = 3 * nbins
+    d = torch.from_numpy(dk).cuda()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        est.compute(d)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = Clocks(local)
+    bsp.bsp_set_profiling(est.plan, True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        est.compute(d)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    phase, ncalls, launches = bsp.bsp_phase_times(est.plan)
+    bsp.bsp_set_profiling(est.plan, False)
+    phase = [p / max(ncalls, 1) for p in phase]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = outputs * world / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(np.ascontiguousarray(dk)).pin_memory()
+        Bh = torch.empty((3, nbins), dtype=torch.float64).pin_memory()
+        est.compute_host(host.numpy(), Bh.numpy())
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            est.compute_host(host.numpy(), Bh.numpy())
+        dt = (time.perf_counter() - t0) / args.steps
+        barrier()
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": outputs * world / dt, "unit": "bins/s", "h2d_bytes_per_step": int(host.numel() * 8),
+               "d2h_bytes_per_step": int(Bh.numel() * 8)}
+
+    # roofline of the dominant phase
+    n3 = float(args.n) ** 3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    fft_ms, con_ms, red_ms = phase
+    if con_ms >= fft_ms:
+        flop = 2.0 * n3 * outputs
+        clk = 2070.0
+        peak = N_SM * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+        ach = flop / (con_ms / 1e3) / 1e12
+        roof = {"kernel": "k_contract_cc (FP32 CUDA-core contraction)", "bound": "alu", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "algorithmic": "2 n^3 flop per (bin, l): %.3e flop per launch" % flop}
+    else:
+        g = fft_alg_bytes(args.n, edges)
+        ach = g / (fft_ms / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "k_pass1/2/3 (filter + inverse FFT)", "bound": "hbm", "achieved": ach, "peak": peak,
+                "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+                "algorithmic": "%.3e bytes per step" % g}
+    line = {"metric": METRIC, "value": value, "unit": "bins/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "split_bf16": "bf16x3", "bf16": "bf16"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": desc, "bins": nbins, "outputs": outputs, "precision": args.prec,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (delta(k) %.0f MB, fields %.0f GB)"
+                             % (dk.nbytes / 1e6, 3 * args.shells * n3 * 4 / 1e9),
+                       "counts_s": round(t_counts, 3)},
+            "phases_ms": {"filter_fft": fft_ms, "contraction": con_ms, "reduce": red_ms},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": ck}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        info = cpu_sample(dk, args.n, edges)
+        step_s = info["t_full"] + 3 * args.shells * info["t_field"] + outputs * info["t_bin"]
+        line["cpu_baseline"] = {"value": outputs / step_s, "unit": "bins/s", "cores": info["cores"],
+                                "kind": "oracle", "sample": info["sample"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    est.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def fft_alg_bytes(n, edges):
+    """Algorithmic HBM bytes of the filter + inverse FFT phase per step: per
+    field, the nonzero input modes it reads (complex64), the pruned
+    intermediates written and read once (complex64), and the real output."""
+    K = 0
+    emax = edges[-1]
+    while (K + 1) ** 2 < emax ** 2:
+        K += 1
+    nK = min(n, 2 * K + 1)
+    nKz = min(n // 2 + 1, K + 1)
+    nf = 3 * (len(edges) - 1)
+    per = 8 * (nK * nK * nKz) + 2 * 8 * (nK * n * nKz) + 2 * 8 * (n * n * nKz) + 4 * n ** 3
+    return float(nf * per)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -143,6 +143,18 @@ bsp_status bsp_host_staging_size(const bsp_plan* plan, size_t* bytes);
  * [n_ell][n_bins], device), copied into T (device).  For tests. */
 bsp_status bsp_last_raw(const bsp_plan* plan, void* ws, void* stream, double* T);
 
+/*
+ * Per-phase device timing of bsp_compute with CUDA events recorded on the
+ * caller's stream (off by default; the events add no work).
+ * bsp_phase_times waits for the last recorded event and returns the summed
+ * milliseconds since profiling was switched on or last read:
+ * ms[0] filter + inverse FFTs, ms[1] contraction, ms[2] reduction and
+ * normalisation; *ncalls profiled calls; *launches kernel launches of one
+ * bsp_compute.  Reading resets the sums.
+ */
+bsp_status bsp_set_profiling(bsp_plan* plan, int on);
+bsp_status bsp_phase_times(bsp_plan* plan, double* ms, int* ncalls, int* launches);
+
 /* Human-readable text for a status, and the last CUDA error text seen by
  * this thread ("" if none). */
 const char* bsp_status_string(int status);

@@ -183,13 +183,19 @@ def full_from_half(half: np.ndarray, n: int) -> np.ndarray:
     computes changes; self-conjugate points keep their real part only."""
     h = np.asarray(half, dtype=np.complex128)
     assert h.shape == (n, n, n // 2 + 1)
+
+    def negate(a, axis):
+        # index j -> (-j) mod n along `axis`
+        return np.roll(np.flip(a, axis=axis), 1, axis=axis)
+
     full = np.empty((n, n, n), dtype=np.complex128)
     full[:, :, : n // 2 + 1] = h
-    neg = (-np.arange(n)) % n
-    for kz in range(n // 2 + 1, n):
-        full[:, :, kz] = np.conj(h[neg][:, neg][:, :, n - kz])
-    mirror = np.conj(full[neg][:, neg][:, :, neg])
-    return 0.5 * (full + mirror)
+    # n_z in (n/2, n): delta(nx, ny, nz) = conj delta(-nx, -ny, n - nz)
+    full[:, :, n // 2 + 1:] = np.conj(negate(negate(h, 0), 1)[:, :, 1: n // 2][:, :, ::-1])
+    mirror = np.conj(negate(negate(negate(full, 0), 1), 2))
+    full += mirror
+    full *= 0.5
+    return full
 
 
 def real_field(full: np.ndarray, weight: np.ndarray) -> np.ndarray:

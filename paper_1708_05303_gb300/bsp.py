@@ -35,6 +35,9 @@ _SIGS = [
     ("bsp_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_compute_host", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_last_raw", ctypes.c_int, [_P, _P, _P, _P]),
+    ("bsp_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
+    ("bsp_phase_times", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]),
     ("bsp_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("bsp_last_error", ctypes.c_char_p, []),
     ("bsp_version", ctypes.c_int, []),
@@ -148,6 +151,18 @@ def bsp_compute_host(plan: int, delta_k_host: np.ndarray, B_host: np.ndarray, ws
 
 def bsp_last_raw(plan: int, ws, T, stream=None):
     _check(load().bsp_last_raw(plan, _dptr(ws), _stream_handle(stream), _dptr(T)), "bsp_last_raw")
+
+
+def bsp_set_profiling(plan: int, on: bool):
+    _check(load().bsp_set_profiling(plan, int(bool(on))), "bsp_set_profiling")
+
+
+def bsp_phase_times(plan: int):
+    """(ms[3] = filter+FFT, contraction, reduction summed over calls; ncalls; launches per call)."""
+    ms = (ctypes.c_double * 3)()
+    nc, nl = ctypes.c_int(), ctypes.c_int()
+    _check(load().bsp_phase_times(plan, ms, ctypes.byref(nc), ctypes.byref(nl)), "bsp_phase_times")
+    return list(ms), nc.value, nl.value
 
 
 def bsp_version() -> int:

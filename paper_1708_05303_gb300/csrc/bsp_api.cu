@@ -21,6 +21,7 @@ using namespace bsp;
 namespace {
 
 thread_local std::string g_last_error;
+constexpr int CCOLS = 64;   // pairs per CUDA-core contraction tile (bsp_contract.cu)
 
 bsp_status cuda_fail(cudaError_t e, const char* where) {
     g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
@@ -75,11 +76,11 @@ struct HostSched {
 
 typedef std::vector<std::array<int, 3>> BinList;
 
-// Tiles of <= 128 pairs (b, c) (sorted by b, then c; the shells they touch
+// Tiles of <= `cols` pairs (b, c) (sorted by b, then c; the shells they touch
 // span <= 64), each with the rows (slot, a) for a in the tile's a-range, cut
 // into chunks of <= 64 rows.
 HostSched build_sched(const BinList& bins, const std::vector<int>& out_slots, int nsh, size_t npts,
-                      int target_ctas) {
+                      int target_ctas, int cols) {
     HostSched h;
     std::map<std::pair<int, int>, int> pidx;
     for (auto& t : bins) pidx[{t[1], t[2]}] = 0;
@@ -99,7 +100,7 @@ HostSched build_sched(const BinList& bins, const std::vector<int>& out_slots, in
     while (i < pl.size()) {
         int p0 = (int)i, slo = pl[i].second, shi = pl[i].first, lo = alo[i], hi = ahi[i];
         size_t j = i + 1;
-        while (j < pl.size() && (int)(j - i) < 128) {
+        while (j < pl.size() && (int)(j - i) < cols) {
             int nslo = std::min(slo, pl[j].second), nshi = std::max(shi, pl[j].first);
             if (nshi - nslo + 1 > 64) break;
             slo = nslo; shi = nshi;
@@ -169,8 +170,8 @@ bsp_status upload_sched(DevSched& d, const HostSched& h) {
     return BSP_OK;
 }
 
-size_t partial_bytes(const HostSched& h) {
-    return (size_t)h.works.size() * h.nsplit * 64 * 128 * sizeof(double);
+size_t partial_bytes(const HostSched& h, int cols) {
+    return (size_t)h.works.size() * h.nsplit * 64 * cols * sizeof(double);
 }
 
 }  // namespace
@@ -207,8 +208,14 @@ struct bsp_plan {
     int fb32 = 1, fb64 = 1;
     size_t part_bytes = 0, tout_bytes = 0, cnt_out_bytes = 0;
     size_t ws_bytes = 0, staging_bytes = 0;
+    // optional per-phase CUDA-event timing of bsp_compute
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;      // 4 events per profiled call
+    size_t ev_used = 0;
+    int launches_last = 0;
 
     ~bsp_plan() {
+        for (auto e : ev_pool) cudaEventDestroy(e);
         cudaFree(d_shell_of); cudaFree(d_tw32); cudaFree(d_tw64);
         cudaFree(d_fd_delta); cudaFree(d_fd_unit); cudaFree(d_counts);
         cand_dev.release(); comp_dev.release();
@@ -252,7 +259,7 @@ Layout layout_counts(const bsp_plan* p) {
     L.t1 = L.fields + p->fld64_bytes;
     L.t2 = L.t1 + t1 * p->fb64;
     L.partial = L.t2 + t2 * p->fb64;
-    L.tout = L.partial + round256(partial_bytes(p->cand_sched));
+    L.tout = L.partial + round256(partial_bytes(p->cand_sched, CCOLS));
     L.cnt = L.tout;
     L.end = L.cnt + p->cnt_out_bytes;
     return L;
@@ -371,13 +378,13 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
                 if (e[a] < e[b + 1] + e[c + 1] || e[a + 1] + e[b + 1] + e[c + 1] > n)
                     p->cand.push_back({a, b, c});
             }
-    p->cand_sched = build_sched(p->cand, std::vector<int>{0}, n_shells, p->npts(), p->target_ctas);
+    p->cand_sched = build_sched(p->cand, std::vector<int>{0}, n_shells, p->npts(), p->target_ctas, CCOLS);
     if ((st = upload_sched(p->cand_dev, p->cand_sched)) != BSP_OK) {
         delete p;
         return st;
     }
     // workspace sizing: compute schedule bounded by the candidate bins
-    HostSched bound = build_sched(p->cand, p->out_slots, n_shells, p->npts(), p->target_ctas);
+    HostSched bound = build_sched(p->cand, p->out_slots, n_shells, p->npts(), p->target_ctas, CCOLS);
     size_t t1, t2;
     t12_sizes(g, sizeof(float), &t1, &t2);
     const size_t nfields32 = (size_t)p->nslot() * n_shells;
@@ -388,8 +395,8 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     p->fb64 = (int)std::max<size_t>(1, std::min<size_t>(n_shells, (size_t)(2ull << 30) / (t1 + t2)));
     // the valid-bin schedule has at most as many works as the bound, and
     // nsplit <= ceil(target / nwork), so nwork * nsplit <= target + nwork
-    p->part_bytes = round256(std::max(partial_bytes(bound),
-                                      (size_t)(p->target_ctas + bound.works.size()) * 64 * 128 * sizeof(double)));
+    p->part_bytes = round256(std::max(partial_bytes(bound, CCOLS),
+                                      (size_t)(p->target_ctas + bound.works.size()) * 64 * CCOLS * sizeof(double)));
     p->tout_bytes = round256(p->ells.size() * p->cand.size() * sizeof(double));
     p->cnt_out_bytes = round256(p->cand.size() * sizeof(double));
     p->ws_bytes = std::max(layout_compute(p).end, layout_counts(p).end);
@@ -449,8 +456,8 @@ bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
             p->bins.push_back(p->cand[i]);
             p->counts.push_back(hc[i]);
         }
-    p->comp_sched = build_sched(p->bins, p->out_slots, p->nsh, p->npts(), p->target_ctas);
-    if (round256(partial_bytes(p->comp_sched)) > p->part_bytes) return BSP_ENOMEM;
+    p->comp_sched = build_sched(p->bins, p->out_slots, p->nsh, p->npts(), p->target_ctas, CCOLS);
+    if (round256(partial_bytes(p->comp_sched, CCOLS)) > p->part_bytes) return BSP_ENOMEM;
     bsp_status s = upload_sched(p->comp_dev, p->comp_sched);
     if (s != BSP_OK) return s;
     cudaFree(p->d_counts);
@@ -472,9 +479,26 @@ bsp_status bsp_plan_bins(const bsp_plan* p, int* n_bins, int32_t* abc, double* c
     return BSP_OK;
 }
 
+static bsp_status mark(bsp_plan* p, cudaStream_t st, int k) {
+    if (!p->profiling) return BSP_OK;
+    size_t need = p->ev_used + 1;
+    while (p->ev_pool.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        p->ev_pool.push_back(e);
+    }
+    (void)k;
+    CK(cudaEventRecord(p->ev_pool[p->ev_used++], st));
+    return BSP_OK;
+}
+
 static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, void* ws, cudaStream_t st,
                                double* B) {
     if (nbar != 0.0) return BSP_EUNSUPPORTED;
+    if (p->profiling && p->ev_used % 4 != 0) return BSP_ESTATE;
+    bsp_status ms;
+    if ((ms = mark(p, st, 0)) != BSP_OK) return ms;
+    int launches = 0;
     const Layout L = layout_compute(p);
     char* base = (char*)ws;
     float* f32 = (float*)(base + L.fields);
@@ -487,17 +511,22 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
                                                  p->d_fd_delta + f0, nb, p->d_tw32, t1, t2,
                                                  f32 + (size_t)f0 * p->npts(), p->npts(), st);
         if (e != cudaSuccess) return cuda_fail(e, "fft");
+        launches += 3;
     }
+    if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
     double* partial = (double*)(base + L.partial);
     double* tout = (double*)(base + L.tout);
     cudaError_t e = launch_contract_cc<float>(f32, p->npts(), p->comp_dev.works, p->comp_dev.nwork,
                                               p->comp_dev.pairs, p->comp_dev.rowf, p->npts(),
                                               p->comp_dev.nsplit, partial, st);
     if (e != cudaSuccess) return cuda_fail(e, "contract");
+    if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
     const double V = p->box * p->box * p->box;
     e = launch_reduce(partial, p->comp_dev.nsplit, p->comp_dev.loc, p->comp_dev.nloc, (int)p->bins.size(),
                       p->d_counts, 1.0 / (V * (double)p->npts()), 1, tout, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    if ((ms = mark(p, st, 3)) != BSP_OK) return ms;
+    p->launches_last = launches + 2;
     return BSP_OK;
 }
 
@@ -524,6 +553,30 @@ bsp_status bsp_compute_host(bsp_plan* p, const void* delta_k_host, double nbar, 
     CK(cudaMemcpyAsync(B_host, Bdev, sizeof(double) * p->ells.size() * p->bins.size(), cudaMemcpyDeviceToHost,
                        st));
     CK(cudaStreamSynchronize(st));
+    return BSP_OK;
+}
+
+bsp_status bsp_set_profiling(bsp_plan* p, int on) {
+    if (!p) return BSP_EINVAL;
+    p->profiling = on != 0;
+    p->ev_used = 0;
+    return BSP_OK;
+}
+
+bsp_status bsp_phase_times(bsp_plan* p, double* ms, int* ncalls, int* launches) {
+    if (!p || !ms) return BSP_EINVAL;
+    ms[0] = ms[1] = ms[2] = 0.0;
+    const size_t calls = p->ev_used / 4;
+    if (calls) CK(cudaEventSynchronize(p->ev_pool[4 * calls - 1]));
+    for (size_t c = 0; c < calls; ++c)
+        for (int k = 0; k < 3; ++k) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, p->ev_pool[4 * c + k], p->ev_pool[4 * c + k + 1]));
+            ms[k] += t;
+        }
+    if (ncalls) *ncalls = (int)calls;
+    if (launches) *launches = p->launches_last;
+    p->ev_used = 0;
     return BSP_OK;
 }
 

@@ -5,11 +5,12 @@
 //   T^l[a; b, c] = sum_x F^l_a(x) F^0_b(x) F^0_c(x),
 // is organised as a matrix product over x: rows r = (l, a), columns
 // p = pairs (b, c), T[r][p] = sum_x A_r(x) P_p(x) with P_p = F^0_b F^0_c formed
-// once per x and shared by every (l, a).  A work item is a tile of <= 128
+// once per x and shared by every (l, a).  A work item is a tile of <= 64
 // pairs times <= 64 rows; a CTA owns one work item and one contiguous
-// x-segment, keeps 4 x 8 outputs per thread in registers, and flushes them
-// into its own FP64 partial slot every FLUSH points (the FP32 path) so that
-// FP32 accumulation never runs over more than FLUSH terms.  The reduction
+// x-segment and keeps 4 x 4 outputs per thread in registers.  FP32 sums run
+// over at most 64 points; each such block sum is folded into a compensated
+// (TwoSum hi + lo) FP32 pair, so the segment sum is accurate to ~eps times
+// the block error, and written once to the CTA's own FP64 slot.  The reduction
 // sums the per-segment partials in a fixed order in FP64 (deterministic),
 // then normalises: B = T / (V n^3 N_abc) or N_abc = rint(T / n^3).
 #include "bsp_internal.h"
@@ -20,38 +21,42 @@ namespace {
 
 constexpr int CC_THREADS = 256;
 constexpr int CC_ROWS = 64;
-constexpr int CC_COLS = 128;
+constexpr int CC_COLS = 64;
+constexpr int CC_OUT = CC_ROWS * CC_COLS;
 
 template <typename R>
 struct CCCfg;
 template <>
 struct CCCfg<float> {
-    static constexpr int XC = 32;
-    static constexpr int FLUSH = 8192;
+    static constexpr int XC = 32;       // x-points staged per step
+    static constexpr int BLOCK = 2;     // steps summed in plain FP32 before the compensated fold
 };
 template <>
 struct CCCfg<double> {
     static constexpr int XC = 16;
-    static constexpr int FLUSH = 1 << 30;
+    static constexpr int BLOCK = 1;
 };
 
-template <typename R, int N>
-struct Vec;
+template <typename R>
+__device__ __forceinline__ void ld4(const R* p, R* v);
 template <>
-struct Vec<float, 4> {
-    static __device__ __forceinline__ void ld(const float* p, float* v) {
-        float4 t = *reinterpret_cast<const float4*>(p);
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    }
-};
+__device__ __forceinline__ void ld4<float>(const float* p, float* v) {
+    float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
 template <>
-struct Vec<double, 4> {
-    static __device__ __forceinline__ void ld(const double* p, double* v) {
-        double2 t0 = reinterpret_cast<const double2*>(p)[0];
-        double2 t1 = reinterpret_cast<const double2*>(p)[1];
-        v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
-    }
-};
+__device__ __forceinline__ void ld4<double>(const double* p, double* v) {
+    double2 t0 = reinterpret_cast<const double2*>(p)[0];
+    double2 t1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+
+// Error-free sum: s + e = a + b exactly (Knuth's TwoSum, no ordering needed).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
 
 template <typename R>
 __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict__ fields, size_t fstride,
@@ -61,8 +66,9 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
                                                             size_t npts, size_t seg,
                                                             double* __restrict__ partial) {
     constexpr int XC = CCCfg<R>::XC;
-    constexpr int FLUSH = CCCfg<R>::FLUSH;
-    constexpr int AS = CC_ROWS + 4;   // padded row strides (multiples of 16 bytes)
+    constexpr int BLOCK = CCCfg<R>::BLOCK;
+    constexpr bool COMP = sizeof(R) == 4;   // compensated FP32 accumulation
+    constexpr int AS = CC_ROWS + 4;         // padded row strides (multiples of 16 bytes)
     constexpr int PS = CC_COLS + 4;
     __shared__ __align__(16) R As[XC][AS];
     __shared__ __align__(16) R Ps[XC][PS];
@@ -73,7 +79,7 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
     const Work w = works[blockIdx.x];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ty = (warp & 1) * 8 + (lane >> 2);     // rows 4*ty .. 4*ty+3
-    const int tx = (warp >> 1) * 4 + (lane & 3);     // cols 8*tx .. 8*tx+7
+    const int tx = (warp >> 1) * 4 + (lane & 3);     // cols 4*tx .. 4*tx+3
     for (int i = tid; i < CC_COLS; i += CC_THREADS) {
         int2 v = {-1, -1};
         if (i < w.npairs) {
@@ -87,26 +93,13 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
 
     const size_t x_begin = (size_t)blockIdx.y * seg;
     const size_t x_end = min(npts, x_begin + seg);
-    double* slot = partial + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (CC_ROWS * CC_COLS);
 
-    R acc[4][8];
+    R acc[4][4], hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = (R)0;
-    bool first = true;
-    size_t since_flush = 0;
-    auto flush = [&]() {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                double* d = slot + (size_t)(ty * 4 + i) * CC_COLS + tx * 8 + j;
-                *d = first ? (double)acc[i][j] : *d + (double)acc[i][j];
-                acc[i][j] = (R)0;
-            }
-        first = false;
-    };
+        for (int j = 0; j < 4; ++j) acc[i][j] = hi[i][j] = lo[i][j] = (R)0;
+    int step = 0;
     __syncthreads();
 
     for (size_t x0 = x_begin; x0 < x_end; x0 += XC) {
@@ -129,23 +122,36 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
         __syncthreads();
 #pragma unroll 4
         for (int x = 0; x < XC; ++x) {
-            R a[4], p[8];
-            Vec<R, 4>::ld(&As[x][ty * 4], a);
-            Vec<R, 4>::ld(&Ps[x][tx * 8], p);
-            Vec<R, 4>::ld(&Ps[x][tx * 8 + 4], p + 4);
+            R a[4], p[4];
+            ld4<R>(&As[x][ty * 4], a);
+            ld4<R>(&Ps[x][tx * 4], p);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], p[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], p[j], acc[i][j]);
         }
         __syncthreads();
-        since_flush += XC;
-        if (since_flush >= (size_t)FLUSH) {
-            flush();
-            since_flush = 0;
+        if (COMP && ++step == BLOCK) {
+            step = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float s, e;
+                    two_sum((float)hi[i][j], (float)acc[i][j], s, e);
+                    hi[i][j] = (R)s;
+                    lo[i][j] += (R)e;
+                    acc[i][j] = (R)0;
+                }
         }
     }
-    flush();
+    double* slot = partial + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * CC_OUT;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            slot[(size_t)(ty * 4 + i) * CC_COLS + tx * 4 + j] =
+                (double)acc[i][j] + (double)hi[i][j] + (double)lo[i][j];
 }
 
 __global__ void k_reduce(const double* __restrict__ partial, int nsplit, const BinLoc* __restrict__ loc,
@@ -154,9 +160,9 @@ __global__ void k_reduce(const double* __restrict__ partial, int nsplit, const B
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nout) return;
     const BinLoc L = loc[i];
-    const double* p = partial + (size_t)L.work * nsplit * (CC_ROWS * CC_COLS) + (size_t)L.row * CC_COLS + L.col;
+    const double* p = partial + (size_t)L.work * nsplit * CC_OUT + (size_t)L.row * CC_COLS + L.col;
     double s = 0.0;
-    for (int k = 0; k < nsplit; ++k) s += p[(size_t)k * (CC_ROWS * CC_COLS)];
+    for (int k = 0; k < nsplit; ++k) s += p[(size_t)k * CC_OUT];
     if (T_out) T_out[i] = s;
     if (mode == 0) out[i] = rint(s * scale);
     else out[i] = s * scale / counts[i % nbins];
