@@ -70,7 +70,9 @@ typedef enum {
 typedef enum {
     BSP_FP32 = 0,        /* CUDA-core FP32 FMA, FP32 partials flushed to FP64 */
     BSP_SPLIT_BF16 = 1,  /* tcgen05 BF16 hi+lo split products, FP32 accumulate */
-    BSP_BF16 = 2         /* tcgen05 BF16 hi only (reported, not gated) */
+    BSP_BF16 = 2,        /* tcgen05 BF16 hi only (reported, not gated) */
+    BSP_SPLIT_F16 = 3    /* tcgen05 FP16 hi+lo split products of power-of-two scaled
+                            operands (22 significant bits), FP32 accumulate */
 } bsp_precision;
 
 typedef struct bsp_plan bsp_plan;
@@ -142,6 +144,30 @@ bsp_status bsp_host_staging_size(const bsp_plan* plan, size_t* bytes);
 /* Raw sums T^l = sum_x F^l_a F_b F_c of the last bsp_compute (FP64
  * [n_ell][n_bins], device), copied into T (device).  For tests. */
 bsp_status bsp_last_raw(const bsp_plan* plan, void* ws, void* stream, double* T);
+
+/*
+ * Schedule statistics after bsp_counts, for roofline accounting:
+ * st[0] multiply-adds issued per x-point by the contraction (all tiles,
+ * all split products), st[1] useful multiply-adds per x-point (n_ell x
+ * n_bins), st[2] work items (tiles), st[3] x-segments per work item.
+ */
+bsp_status bsp_plan_stats(const bsp_plan* plan, double* st);
+
+/*
+ * Tensor-core paths only: the number of x-points (a multiple of 64, 64 ..
+ * 2^20; default 1024) summed in an FP32 tensor-memory accumulator before it
+ * is folded into the compensated running sums.  Shorter chunks are more
+ * accurate and cost more epilogue work.
+ */
+bsp_status bsp_set_accumulation_chunk(bsp_plan* plan, int points);
+
+/*
+ * Error word of the plan's kernels: 0 if no kernel has reported a problem,
+ * else a bit mask of bounded waits that gave up (the kernel then stopped
+ * early, released its tensor memory and left its outputs undefined).
+ * Synchronous (waits for the device).  Returns BSP_ETIMEOUT if nonzero.
+ */
+bsp_status bsp_device_status(bsp_plan* plan, int* code);
 
 /*
  * Per-phase device timing of bsp_compute with CUDA events recorded on the

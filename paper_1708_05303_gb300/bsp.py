@@ -18,8 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libbsp.so")
 
 BSP_OK, BSP_EINVAL, BSP_ENOMEM, BSP_ECUDA, BSP_EUNSUPPORTED, BSP_ETIMEOUT, BSP_ESTATE = 0, -1, -2, -3, -4, -5, -6
-BSP_FP32, BSP_SPLIT_BF16, BSP_BF16 = 0, 1, 2
-PRECISIONS = {"fp32": BSP_FP32, "split_bf16": BSP_SPLIT_BF16, "bf16": BSP_BF16}
+BSP_FP32, BSP_SPLIT_BF16, BSP_BF16, BSP_SPLIT_F16 = 0, 1, 2, 3
+PRECISIONS = {"fp32": BSP_FP32, "split_bf16": BSP_SPLIT_BF16, "bf16": BSP_BF16, "split_f16": BSP_SPLIT_F16}
 
 # (name, restype, argtypes) of every exported entry point declared in include/bsp.h
 _P = ctypes.c_void_p
@@ -35,6 +35,9 @@ _SIGS = [
     ("bsp_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_compute_host", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_last_raw", ctypes.c_int, [_P, _P, _P, _P]),
+    ("bsp_device_status", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    ("bsp_set_accumulation_chunk", ctypes.c_int, [_P, ctypes.c_int]),
+    ("bsp_plan_stats", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("bsp_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
     ("bsp_phase_times", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int)]),
@@ -151,6 +154,26 @@ def bsp_compute_host(plan: int, delta_k_host: np.ndarray, B_host: np.ndarray, ws
 
 def bsp_last_raw(plan: int, ws, T, stream=None):
     _check(load().bsp_last_raw(plan, _dptr(ws), _stream_handle(stream), _dptr(T)), "bsp_last_raw")
+
+
+def bsp_device_status(plan: int) -> int:
+    """The plan's device error word (0 = no kernel reported a problem)."""
+    v = ctypes.c_int()
+    st = load().bsp_device_status(plan, ctypes.byref(v))
+    if st not in (BSP_OK, BSP_ETIMEOUT):
+        _check(st, "bsp_device_status")
+    return v.value
+
+
+def bsp_plan_stats(plan: int) -> dict:
+    st = (ctypes.c_double * 4)()
+    _check(load().bsp_plan_stats(plan, st), "bsp_plan_stats")
+    return {"issued_macs_per_point": st[0], "useful_macs_per_point": st[1], "works": int(st[2]),
+            "nsplit": int(st[3])}
+
+
+def bsp_set_accumulation_chunk(plan: int, points: int):
+    _check(load().bsp_set_accumulation_chunk(plan, int(points)), "bsp_set_accumulation_chunk")
 
 
 def bsp_set_profiling(plan: int, on: bool):

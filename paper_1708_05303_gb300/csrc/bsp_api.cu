@@ -1,6 +1,7 @@
 // bsp_api.cu -- the C ABI of libbsp (include/bsp.h): plan creation, argument
 // checks, workspace layout, scheduling of the contraction tiles, and the
 // host orchestration of filter -> inverse FFT -> contraction -> reduction.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -174,6 +175,121 @@ size_t partial_bytes(const HostSched& h, int cols) {
     return (size_t)h.works.size() * h.nsplit * 64 * cols * sizeof(double);
 }
 
+// Tensor-core schedule: tiles of <= 128 pairs (sorted by (b, c), shells
+// spanned <= 64); each tile's rows are the fields (slot, a) for a in the
+// tile's a-range, in boxes of 8 consecutive fields, <= 16 boxes (N <= 128)
+// per work item.
+struct TcSched {
+    std::vector<TcWork> works;
+    std::vector<int2> pairs;
+    std::vector<BinLoc> loc;
+    int nsplit = 1;
+};
+
+TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, int nsh, size_t npts) {
+    TcSched h;
+    std::map<std::pair<int, int>, int> pidx;
+    for (auto& t : bins) pidx[{t[1], t[2]}] = 0;
+    std::vector<std::pair<int, int>> pl;
+    for (auto& kv : pidx) pl.push_back(kv.first);
+    for (size_t i = 0; i < pl.size(); ++i) pidx[pl[i]] = (int)i;
+    std::vector<int> alo(pl.size(), 1 << 30), ahi(pl.size(), -1);
+    for (auto& t : bins) {
+        int p = pidx[{t[1], t[2]}];
+        alo[p] = std::min(alo[p], t[0]);
+        ahi[p] = std::max(ahi[p], t[0]);
+    }
+    // per pair: (tile first work, tile a_lo, boxes per slot, pair index within tile)
+    struct TileRef { int work0, alo, nbs, p0; };
+    std::vector<TileRef> ref(pl.size());
+    size_t i = 0;
+    while (i < pl.size()) {
+        int slo = pl[i].second, shi = pl[i].first, lo = alo[i], hi = ahi[i];
+        size_t j = i + 1;
+        while (j < pl.size() && (int)(j - i) < 128) {
+            int nslo = std::min(slo, pl[j].second), nshi = std::max(shi, pl[j].first);
+            if (nshi - nslo + 1 > 64) break;
+            slo = nslo; shi = nshi;
+            lo = std::min(lo, alo[j]); hi = std::max(hi, ahi[j]);
+            ++j;
+        }
+        const int na = hi - lo + 1, nbs = (na + 7) / 8;
+        std::vector<int> boxes;
+        for (int si : out_slots)
+            for (int b = 0; b < nbs; ++b) boxes.push_back(si * nsh + lo + 8 * b);
+        const int work0 = (int)h.works.size();
+        for (size_t b0 = 0; b0 < boxes.size(); b0 += 16) {
+            TcWork w{};
+            w.pair0 = (int)i;
+            w.npairs = (int)(j - i);
+            w.shell_lo = slo;
+            w.nshell = shi - slo + 1;
+            w.nbox = (int)std::min<size_t>(16, boxes.size() - b0);
+            w.n = (8 * w.nbox + 15) / 16 * 16;
+            for (int b = 0; b < w.nbox; ++b) w.box_field[b] = boxes[b0 + b];
+            h.works.push_back(w);
+        }
+        for (size_t p = i; p < j; ++p) ref[p] = TileRef{work0, lo, nbs, (int)i};
+        i = j;
+    }
+    for (auto& p : pl) h.pairs.push_back(int2{p.first, p.second});
+    h.loc.resize(out_slots.size() * bins.size());
+    for (size_t si = 0; si < out_slots.size(); ++si)
+        for (size_t b = 0; b < bins.size(); ++b) {
+            const int p = pidx[{bins[b][1], bins[b][2]}];
+            const TileRef& t = ref[p];
+            const int box = (int)si * t.nbs + (bins[b][0] - t.alo) / 8;
+            h.loc[si * bins.size() + b] = BinLoc{t.work0 + box / 16, p - t.p0, 8 * (box % 16) + (bins[b][0] - t.alo) % 8, 0};
+        }
+    const int nw = std::max<int>(1, (int)h.works.size());
+    const long long nkb = (long long)((npts + 63) / 64);
+    h.nsplit = (int)std::max<long long>(1, std::min<long long>((1216 + nw - 1) / nw, std::max<long long>(1, nkb / 16)));
+    return h;
+}
+
+constexpr size_t TC_UNIT = 128 * 128;   // FP64 partial values per tensor-core CTA
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2-D map over rows x npts elements, box = 64 elements x 8 rows.
+bsp_status encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, size_t esize, size_t rows, size_t npts,
+                      bool swizzle) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        g_last_error = "cuTensorMapEncodeTiled unavailable";
+        return BSP_ECUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)npts, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(npts * esize)};
+    cuuint32_t box[2] = {64, 8};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        g_last_error = "cuTensorMapEncodeTiled failed: " + std::to_string((int)r);
+        return BSP_ECUDA;
+    }
+    return BSP_OK;
+}
+
 }  // namespace
 
 struct bsp_plan {
@@ -203,6 +319,18 @@ struct bsp_plan {
     double* d_counts = nullptr;
     HostSched comp_sched;
     DevSched comp_dev;
+    // tensor-core path
+    bool tc = false;
+    int nprod = 3;
+    FieldDesc* d_fd_tc = nullptr;     // [nslot*nsh]
+    TcSched tc_sched;
+    TcWork* d_tc_works = nullptr;
+    int2* d_tc_pairs = nullptr;
+    BinLoc* d_tc_loc = nullptr;
+    int* d_err = nullptr;
+    unsigned* d_fmax = nullptr;   // per-field magnitude bounds for the 16-bit scaling
+    int chunk_kb = 16;            // K-blocks (64 points each) per FP32 tensor-memory accumulation
+    size_t f0_bytes = 0, plane_bytes = 0, tc_part_bytes = 0;
     // workspace layout
     size_t fld32_bytes = 0, fld64_bytes = 0, t12_bytes32 = 0, t12_bytes64 = 0;
     int fb32 = 1, fb64 = 1;
@@ -218,6 +346,8 @@ struct bsp_plan {
         for (auto e : ev_pool) cudaEventDestroy(e);
         cudaFree(d_shell_of); cudaFree(d_tw32); cudaFree(d_tw64);
         cudaFree(d_fd_delta); cudaFree(d_fd_unit); cudaFree(d_counts);
+        cudaFree(d_fd_tc); cudaFree(d_tc_works); cudaFree(d_tc_pairs); cudaFree(d_tc_loc); cudaFree(d_err);
+        cudaFree(d_fmax);
         cand_dev.release(); comp_dev.release();
     }
     size_t npts() const { return (size_t)n * n * n; }
@@ -242,6 +372,16 @@ Layout layout_compute(const bsp_plan* p) {
     size_t t1, t2;
     t12_sizes(p->geom, sizeof(float), &t1, &t2);
     L.fields = 0;
+    if (p->tc) {
+        // F0 (FP32, nsh fields) | hi planes | lo planes (16-bit, nslot*nsh fields each)
+        L.t1 = L.fields + p->f0_bytes + 2 * p->plane_bytes;
+        L.t2 = L.t1 + t1 * p->fb32;
+        L.partial = L.t2 + t2 * p->fb32;
+        L.tout = L.partial + p->tc_part_bytes;
+        L.cnt = L.tout + p->tout_bytes;
+        L.end = L.cnt;
+        return L;
+    }
     L.t1 = L.fields + p->fld32_bytes;
     L.t2 = L.t1 + t1 * p->fb32;
     L.partial = L.t2 + t2 * p->fb32;
@@ -309,7 +449,8 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
         if (ells[i] != 0 && ells[i] != 2 && ells[i] != 4) return BSP_EINVAL;
         if (i && ells[i] <= ells[i - 1]) return BSP_EINVAL;
     }
-    if (prec != BSP_FP32) return BSP_EUNSUPPORTED;
+    if (prec != BSP_FP32 && prec != BSP_SPLIT_BF16 && prec != BSP_BF16 && prec != BSP_SPLIT_F16)
+        return BSP_EUNSUPPORTED;
 
     bsp_plan* p = new (std::nothrow) bsp_plan();
     if (!p) return BSP_ENOMEM;
@@ -319,6 +460,8 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     p->edges.assign(edges_kf, edges_kf + n_shells + 1);
     p->ells.assign(ells, ells + n_ell);
     p->prec = prec;
+    p->tc = prec != BSP_FP32;
+    p->nprod = prec == BSP_BF16 ? 1 : 3;
     p->slot_ell.push_back(0);
     for (int l : p->ells)
         if (l != 0) p->slot_ell.push_back(l);
@@ -358,13 +501,20 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
         tw32[t] = {(float)tw64[t].re, (float)tw64[t].im};
     }
     std::vector<FieldDesc> fdd, fdu;
+    std::vector<FieldDesc> fdt;
     for (int s = 0; s < p->nslot(); ++s)
-        for (int a = 0; a < n_shells; ++a) fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, 0});
-    for (int a = 0; a < n_shells; ++a) fdu.push_back(FieldDesc{a, 0, FIELD_UNIT, 0});
+        for (int a = 0; a < n_shells; ++a) {
+            const int f = s * n_shells + a;
+            fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, f, -1, {0, 0, 0}});
+            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, s == 0 ? a : -1, f, {0, 0, 0}});
+        }
+    for (int a = 0; a < n_shells; ++a) fdu.push_back(FieldDesc{a, 0, FIELD_UNIT, a, -1, {0, 0, 0}});
     bsp_status st;
     if ((st = upload(&p->d_shell_of, shell_of)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||
         (st = upload(&p->d_tw64, tw64)) != BSP_OK || (st = upload(&p->d_fd_delta, fdd)) != BSP_OK ||
-        (st = upload(&p->d_fd_unit, fdu)) != BSP_OK) {
+        (st = upload(&p->d_fd_unit, fdu)) != BSP_OK || (st = upload(&p->d_fd_tc, fdt)) != BSP_OK ||
+        (st = upload(&p->d_err, std::vector<int>{0})) != BSP_OK ||
+        (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)(p->nslot() + 1) * n_shells, 0u))) != BSP_OK) {
         delete p;
         return st;
     }
@@ -398,6 +548,14 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     p->part_bytes = round256(std::max(partial_bytes(bound, CCOLS),
                                       (size_t)(p->target_ctas + bound.works.size()) * 64 * CCOLS * sizeof(double)));
     p->tout_bytes = round256(p->ells.size() * p->cand.size() * sizeof(double));
+    if (p->tc) {
+        p->f0_bytes = round256((size_t)n_shells * p->npts() * sizeof(float));
+        p->plane_bytes = round256(nfields32 * p->npts() * 2);
+        TcSched tb = build_tc_sched(p->cand, p->out_slots, n_shells, p->npts());
+        p->tc_part_bytes = round256(std::max<size_t>((size_t)(1216 + tb.works.size()),
+                                                     tb.works.size() * (size_t)tb.nsplit) *
+                                    TC_UNIT * sizeof(double));
+    }
     p->cnt_out_bytes = round256(p->cand.size() * sizeof(double));
     p->ws_bytes = std::max(layout_compute(p).end, layout_counts(p).end);
     p->staging_bytes = round256((size_t)n * n * (n / 2 + 1) * 8) + p->tout_bytes;
@@ -433,7 +591,8 @@ bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
     for (int f0 = 0; f0 < p->nsh; f0 += p->fb64) {
         int nf = std::min(p->fb64, p->nsh - f0);
         cudaError_t e = launch_fft_fields<double>(p->geom, nullptr, p->d_shell_of, nullptr, p->d_fd_unit + f0, nf,
-                                                  p->d_tw64, t1, t2, f64 + (size_t)f0 * p->npts(), p->npts(), st);
+                                                  p->d_tw64, t1, t2, f64, p->npts(), nullptr, nullptr, 0, nullptr,
+                                                  nullptr, st);
         if (e != cudaSuccess) return cuda_fail(e, "fft (counts)");
     }
     double* partial = (double*)(base + L.partial);
@@ -443,8 +602,8 @@ bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
                                                p->cand_dev.nsplit, partial, st);
     if (e != cudaSuccess) return cuda_fail(e, "contract (counts)");
     const double n3 = (double)p->npts();
-    e = launch_reduce(partial, p->cand_dev.nsplit, p->cand_dev.loc, (int)p->cand.size(), (int)p->cand.size(),
-                      nullptr, 1.0 / n3, 0, nullptr, cnt, st);
+    e = launch_reduce(partial, p->cand_dev.nsplit, 0, 0, p->cand_dev.loc, (int)p->cand.size(),
+                      (int)p->cand.size(), nullptr, 1.0 / n3, 0, nullptr, cnt, st);
     if (e != cudaSuccess) return cuda_fail(e, "reduce (counts)");
     std::vector<double> hc(p->cand.size());
     CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(double) * hc.size(), cudaMemcpyDeviceToHost, st));
@@ -460,6 +619,17 @@ bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
     if (round256(partial_bytes(p->comp_sched, CCOLS)) > p->part_bytes) return BSP_ENOMEM;
     bsp_status s = upload_sched(p->comp_dev, p->comp_sched);
     if (s != BSP_OK) return s;
+    if (p->tc) {
+        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->nsh, p->npts());
+        if (round256(p->tc_sched.works.size() * (size_t)p->tc_sched.nsplit * TC_UNIT * sizeof(double)) >
+            p->tc_part_bytes)
+            return BSP_ENOMEM;
+        cudaFree(p->d_tc_works); cudaFree(p->d_tc_pairs); cudaFree(p->d_tc_loc);
+        p->d_tc_works = nullptr; p->d_tc_pairs = nullptr; p->d_tc_loc = nullptr;
+        if ((s = upload(&p->d_tc_works, p->tc_sched.works)) != BSP_OK) return s;
+        if ((s = upload(&p->d_tc_pairs, p->tc_sched.pairs)) != BSP_OK) return s;
+        if ((s = upload(&p->d_tc_loc, p->tc_sched.loc)) != BSP_OK) return s;
+    }
     cudaFree(p->d_counts);
     p->d_counts = nullptr;
     if ((s = upload(&p->d_counts, p->counts)) != BSP_OK) return s;
@@ -501,6 +671,50 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
     int launches = 0;
     const Layout L = layout_compute(p);
     char* base = (char*)ws;
+    if (p->tc) {
+        float* f0 = (float*)(base + L.fields);
+        uint32_t* hi = (uint32_t*)(base + L.fields + p->f0_bytes);
+        uint32_t* lo = (uint32_t*)(base + L.fields + p->f0_bytes + p->plane_bytes);
+        cx<float>* t1 = (cx<float>*)(base + L.t1);
+        cx<float>* t2 = (cx<float>*)(base + L.t2);
+        const int nf = p->nslot() * p->nsh;
+        unsigned* fmax2 = p->d_fmax;              // [nf]  max |T2| per field (bounds |F|)
+        unsigned* f0max = p->d_fmax + nf;         // [nsh] exact max |F0| per shell
+        CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * (nf + p->nsh), st));
+        CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st));
+        const int f16 = p->prec == BSP_SPLIT_F16 ? 1 : 0;
+        for (int f0i = 0; f0i < nf; f0i += p->fb32) {
+            int nb = std::min(p->fb32, nf - f0i);
+            cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, p->d_shell_of, nullptr,
+                                                     p->d_fd_tc + f0i, nb, p->d_tw32, t1, t2, f0, p->npts(), hi,
+                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, f0max, st);
+            if (e != cudaSuccess) return cuda_fail(e, "fft");
+            launches += 3;
+        }
+        if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
+        CUtensorMap tmf0, tmhi, tmlo;
+        bsp_status es;
+        const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        if ((es = encode_map(&tmf0, f0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->nsh, p->npts(), false)) != BSP_OK ||
+            (es = encode_map(&tmhi, hi, t16, 2, nf, p->npts(), true)) != BSP_OK ||
+            (es = encode_map(&tmlo, p->nprod == 3 ? (void*)lo : (void*)hi, t16, 2, nf, p->npts(), true)) != BSP_OK)
+            return es;
+        double* partial = (double*)(base + L.partial);
+        double* tout = (double*)(base + L.tout);
+        cudaError_t e = launch_contract_tc(f16 != 0, &tmf0, &tmhi, &tmlo, p->d_tc_works,
+                                           (int)p->tc_sched.works.size(), p->d_tc_pairs, f0max, fmax2,
+                                           2.f * (float)p->geom.nKz, p->npts(), p->tc_sched.nsplit, p->nprod,
+                                           p->chunk_kb, partial, p->d_err, st);
+        if (e != cudaSuccess) return cuda_fail(e, "contract (tensor cores)");
+        if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
+        const double V = p->box * p->box * p->box;
+        e = launch_reduce(partial, p->tc_sched.nsplit, TC_UNIT, 128, p->d_tc_loc, (int)p->tc_sched.loc.size(),
+                          (int)p->bins.size(), p->d_counts, 1.0 / (V * (double)p->npts()), 1, tout, B, st);
+        if (e != cudaSuccess) return cuda_fail(e, "reduce");
+        if ((ms = mark(p, st, 3)) != BSP_OK) return ms;
+        p->launches_last = launches + 2;
+        return BSP_OK;
+    }
     float* f32 = (float*)(base + L.fields);
     cx<float>* t1 = (cx<float>*)(base + L.t1);
     cx<float>* t2 = (cx<float>*)(base + L.t2);
@@ -508,8 +722,8 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
     for (int f0 = 0; f0 < nf; f0 += p->fb32) {
         int nb = std::min(p->fb32, nf - f0);
         cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, p->d_shell_of, nullptr,
-                                                 p->d_fd_delta + f0, nb, p->d_tw32, t1, t2,
-                                                 f32 + (size_t)f0 * p->npts(), p->npts(), st);
+                                                 p->d_fd_delta + f0, nb, p->d_tw32, t1, t2, f32, p->npts(), nullptr,
+                                                 nullptr, 0, nullptr, nullptr, st);
         if (e != cudaSuccess) return cuda_fail(e, "fft");
         launches += 3;
     }
@@ -522,7 +736,7 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
     if (e != cudaSuccess) return cuda_fail(e, "contract");
     if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
     const double V = p->box * p->box * p->box;
-    e = launch_reduce(partial, p->comp_dev.nsplit, p->comp_dev.loc, p->comp_dev.nloc, (int)p->bins.size(),
+    e = launch_reduce(partial, p->comp_dev.nsplit, 0, 0, p->comp_dev.loc, p->comp_dev.nloc, (int)p->bins.size(),
                       p->d_counts, 1.0 / (V * (double)p->npts()), 1, tout, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "reduce");
     if ((ms = mark(p, st, 3)) != BSP_OK) return ms;
@@ -553,6 +767,38 @@ bsp_status bsp_compute_host(bsp_plan* p, const void* delta_k_host, double nbar, 
     CK(cudaMemcpyAsync(B_host, Bdev, sizeof(double) * p->ells.size() * p->bins.size(), cudaMemcpyDeviceToHost,
                        st));
     CK(cudaStreamSynchronize(st));
+    return BSP_OK;
+}
+
+bsp_status bsp_device_status(bsp_plan* p, int* code) {
+    if (!p || !code) return BSP_EINVAL;
+    CK(cudaMemcpy(code, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return *code ? BSP_ETIMEOUT : BSP_OK;
+}
+
+bsp_status bsp_plan_stats(const bsp_plan* p, double* st) {
+    if (!p || !st) return BSP_EINVAL;
+    if (!p->have_counts) return BSP_ESTATE;
+    double issued = 0, works = 0, nsplit = 1;
+    if (p->tc) {
+        for (const TcWork& w : p->tc_sched.works) issued += 128.0 * w.n * p->nprod;
+        works = (double)p->tc_sched.works.size();
+        nsplit = p->tc_sched.nsplit;
+    } else {
+        issued = (double)p->comp_sched.works.size() * 64.0 * 64.0;
+        works = (double)p->comp_sched.works.size();
+        nsplit = p->comp_sched.nsplit;
+    }
+    st[0] = issued;
+    st[1] = (double)p->ells.size() * p->bins.size();
+    st[2] = works;
+    st[3] = nsplit;
+    return BSP_OK;
+}
+
+bsp_status bsp_set_accumulation_chunk(bsp_plan* p, int points) {
+    if (!p || points < 64 || points % 64 || points > (1 << 20)) return BSP_EINVAL;
+    p->chunk_kb = points / 64;
     return BSP_OK;
 }
 

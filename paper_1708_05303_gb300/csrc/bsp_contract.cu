@@ -154,15 +154,15 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
                 (double)acc[i][j] + (double)hi[i][j] + (double)lo[i][j];
 }
 
-__global__ void k_reduce(const double* __restrict__ partial, int nsplit, const BinLoc* __restrict__ loc,
-                         int nout, int nbins, const double* __restrict__ counts, double scale, int mode,
-                         double* __restrict__ T_out, double* __restrict__ out) {
+__global__ void k_reduce(const double* __restrict__ partial, int nsplit, size_t unit, int row_stride,
+                         const BinLoc* __restrict__ loc, int nout, int nbins, const double* __restrict__ counts,
+                         double scale, int mode, double* __restrict__ T_out, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nout) return;
     const BinLoc L = loc[i];
-    const double* p = partial + (size_t)L.work * nsplit * CC_OUT + (size_t)L.row * CC_COLS + L.col;
+    const double* p = partial + (size_t)L.work * nsplit * unit + (size_t)L.row * row_stride + L.col;
     double s = 0.0;
-    for (int k = 0; k < nsplit; ++k) s += p[(size_t)k * CC_OUT];
+    for (int k = 0; k < nsplit; ++k) s += p[(size_t)k * unit];
     if (T_out) T_out[i] = s;
     if (mode == 0) out[i] = rint(s * scale);
     else out[i] = s * scale / counts[i % nbins];
@@ -188,12 +188,14 @@ template cudaError_t launch_contract_cc<float>(const float*, size_t, const Work*
 template cudaError_t launch_contract_cc<double>(const double*, size_t, const Work*, int, const int2*,
                                                 const int*, size_t, int, double*, cudaStream_t);
 
-cudaError_t launch_reduce(const double* partial, int nsplit, const BinLoc* loc, int nout, int nbins,
-                          const double* counts, double scale, int mode, double* T_out, double* out,
-                          cudaStream_t st) {
+cudaError_t launch_reduce(const double* partial, int nsplit, size_t unit, int row_stride, const BinLoc* loc,
+                          int nout, int nbins, const double* counts, double scale, int mode, double* T_out,
+                          double* out, cudaStream_t st) {
     if (nout <= 0) return cudaSuccess;
-    k_reduce<<<(nout + 255) / 256, 256, 0, st>>>(partial, nsplit, loc, nout, nbins, counts, scale, mode, T_out,
-                                                 out);
+    if (unit == 0) unit = CC_OUT;
+    if (row_stride == 0) row_stride = CC_COLS;
+    k_reduce<<<(nout + 255) / 256, 256, 0, st>>>(partial, nsplit, unit, row_stride, loc, nout, nbins, counts, scale,
+                                                 mode, T_out, out);
     return cudaGetLastError();
 }
 

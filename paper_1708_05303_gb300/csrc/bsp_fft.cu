@@ -219,10 +219,26 @@ __global__ void __launch_bounds__(NTHR) k_pass1(FftGeom g, const cx<float>* __re
 }
 
 // Pass 2: inverse DFT along y for P consecutive f_z of one x.
+__device__ __forceinline__ void block_max_to(unsigned* dst, float m) {
+    // m >= 0: the float bit patterns order like the values
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dst, __float_as_uint(m));
+}
+
+// Power of two s with bound * s in [2^14, 2^15): scaled values stay below the
+// FP16 maximum.  Exact, so dividing by s afterwards is exact.
+__device__ __forceinline__ float pow2_scale(float bound) {
+    if (!(bound > 0.f)) return 1.f;
+    int e;
+    frexpf(bound, &e);
+    return ldexpf(1.f, 15 - e);
+}
+
 template <typename R, int P>
 __global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restrict__ t1,
                                                 size_t t1_stride, const cx<R>* __restrict__ twg,
-                                                cx<R>* __restrict__ t2, size_t t2_stride) {
+                                                cx<R>* __restrict__ t2, size_t t2_stride,
+                                                const FieldDesc* __restrict__ fields, unsigned* __restrict__ fmax2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* buf = tw + g.n;
@@ -245,9 +261,18 @@ __global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restri
     __syncthreads();
     const cx<R>* res = fft_pingpong<R, true>(buf, scr, N, P, 1, P, g.rad, g.nrad, tw, 1);
     cx<R>* dst = t2 + (size_t)blockIdx.y * t2_stride;
+    float m = 0.f;
     for (int e = threadIdx.x; e < N * P; e += NTHR) {
         const int p = e % P, y = e / P, kz = kz0 + p;
-        if (kz < g.nKz) dst[((size_t)x * N + y) * g.nKz + kz] = res[y * P + p];
+        if (kz < g.nKz) {
+            const cx<R> v = res[y * P + p];
+            dst[((size_t)x * N + y) * g.nKz + kz] = v;
+            m = fmaxf(m, (float)(fabs(v.re) + fabs(v.im)));
+        }
+    }
+    if (fmax2) {
+        const int f = fields[blockIdx.y].out16;
+        if (f >= 0) block_max_to(fmax2 + f, m);
     }
 }
 
@@ -258,7 +283,11 @@ __global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restri
 template <typename R, int P>
 __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restrict__ t2,
                                                 size_t t2_stride, const cx<R>* __restrict__ twg,
-                                                R* __restrict__ out, size_t out_stride) {
+                                                const FieldDesc* __restrict__ fields, R* __restrict__ out,
+                                                size_t out_stride, uint32_t* __restrict__ hi,
+                                                uint32_t* __restrict__ lo, int f16,
+                                                const unsigned* __restrict__ fmax2,
+                                                unsigned* __restrict__ f0max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* buf = tw + g.n;
@@ -286,11 +315,47 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
     }
     __syncthreads();
     const cx<R>* res = fft_pingpong<R, false>(buf, scr, M, P, ps, 1, g.rad_h, g.nrad_h, tw, 2);
-    R* dst = out + (size_t)blockIdx.y * out_stride;
+    const FieldDesc fd = fields[blockIdx.y];
+    R* dst = fd.out32 >= 0 ? out + (size_t)fd.out32 * out_stride : nullptr;
+    const size_t plane = (size_t)N * N * M;   // 32-bit words (two 16-bit values) per field plane
+    uint32_t* dhi = (fd.out16 >= 0 && hi) ? hi + (size_t)fd.out16 * plane : nullptr;
+    uint32_t* dlo = (fd.out16 >= 0 && lo) ? lo + (size_t)fd.out16 * plane : nullptr;
+    // |F(x,y,z)| <= sum_kz 2 |H_kz| <= 2 nKz max|T2|: the split planes are
+    // scaled by the power of two that keeps that bound below 2^15
+    const float sc = (dhi && fmax2) ? pow2_scale(2.f * (float)g.nKz * __uint_as_float(fmax2[fd.out16])) : 1.f;
+    float mx = 0.f;
     for (int e = threadIdx.x; e < M * P; e += NTHR) {
         const int m = e % M, p = e / M, y = y0 + p;
-        if (y < N) reinterpret_cast<cx<R>*>(dst + ((size_t)x * N + y) * N)[m] = res[p * ps + m];
+        if (y >= N) continue;
+        const size_t pos = ((size_t)x * N + y) * M + m;
+        const cx<R> v = res[p * ps + m];
+        if (dst) {
+            reinterpret_cast<cx<R>*>(dst)[pos] = v;
+            mx = fmaxf(mx, fmaxf(fabsf((float)v.re), fabsf((float)v.im)));
+        }
+        if (dhi) {
+            // two consecutive z values -> 16-bit hi and lo planes (x0 in the low half)
+            const float x0 = (float)v.re * sc, x1 = (float)v.im * sc;
+            uint32_t h, l;
+            if (f16) asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x1), "f"(x0));
+            else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x1), "f"(x0));
+            float h0, h1;
+            if (f16) {
+                unsigned short a = (unsigned short)(h & 0xFFFFu), b = (unsigned short)(h >> 16);
+                asm("cvt.f32.f16 %0, %1;" : "=f"(h0) : "h"(a));
+                asm("cvt.f32.f16 %0, %1;" : "=f"(h1) : "h"(b));
+            } else {
+                h0 = __uint_as_float(h << 16);
+                h1 = __uint_as_float(h & 0xFFFF0000u);
+            }
+            const float r0 = x0 - h0, r1 = x1 - h1;
+            if (f16) asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(r1), "f"(r0));
+            else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(r1), "f"(r0));
+            dhi[pos] = h;
+            if (dlo) dlo[pos] = l;
+        }
     }
+    if (f0max && dst) block_max_to(f0max + fd.out32, mx);
 }
 
 template <typename R>
@@ -310,6 +375,7 @@ template <typename R>
 cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const int16_t* shell_of,
                               const float* radial, const FieldDesc* d_fields, int nfields,
                               const cx<R>* tw, cx<R>* t1, cx<R>* t2, R* out, size_t out_stride,
+                              uint32_t* hi, uint32_t* lo, int f16, unsigned* fmax2, unsigned* f0max,
                               cudaStream_t st) {
     using C = FftCfg<R>;
     const int N = g.n, M = N / 2;
@@ -327,16 +393,19 @@ cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const in
     const int nkzb = (g.nKz + C::P - 1) / C::P;
     dim3 g1(g.nK * nkzb, nfields), g2(N * nkzb, nfields), g3(N * ((N + C::P3 - 1) / C::P3), nfields);
     k_pass1<R, C::P><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);
-    k_pass2<R, C::P><<<g2, NTHR, sm12, st>>>(g, t1, t1_stride, tw, t2, t2_stride);
-    k_pass3<R, C::P3><<<g3, NTHR, sm3, st>>>(g, t2, t2_stride, tw, out, out_stride);
+    k_pass2<R, C::P><<<g2, NTHR, sm12, st>>>(g, t1, t1_stride, tw, t2, t2_stride, d_fields, fmax2);
+    k_pass3<R, C::P3><<<g3, NTHR, sm3, st>>>(g, t2, t2_stride, tw, d_fields, out, out_stride, hi, lo, f16, fmax2,
+                                             f0max);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_fft_fields<float>(const FftGeom&, const cx<float>*, const int16_t*, const float*,
                                               const FieldDesc*, int, const cx<float>*, cx<float>*,
-                                              cx<float>*, float*, size_t, cudaStream_t);
+                                              cx<float>*, float*, size_t, uint32_t*, uint32_t*, int, unsigned*, unsigned*,
+                                              cudaStream_t);
 template cudaError_t launch_fft_fields<double>(const FftGeom&, const cx<float>*, const int16_t*, const float*,
                                                const FieldDesc*, int, const cx<double>*, cx<double>*,
-                                               cx<double>*, double*, size_t, cudaStream_t);
+                                               cx<double>*, double*, size_t, uint32_t*, uint32_t*, int,
+                                               unsigned*, unsigned*, cudaStream_t);
 
 }  // namespace bsp

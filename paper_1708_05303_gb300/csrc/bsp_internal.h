@@ -25,7 +25,9 @@ struct FieldDesc {
     int shell;   // shell index (FIELD_DELTA/UNIT/POWER) or radial table row (FIELD_RADIAL)
     int ell;     // 0, 2, 4
     int kind;    // FieldKind
-    int pad;
+    int out32;   // index of the FP32/FP64 output field, or -1
+    int out16;   // index of the 16-bit hi/lo output planes, or -1
+    int pad[3];
 };
 
 // Geometry of the pruned inverse FFT.  Only frequencies |f| <= K per axis
@@ -56,6 +58,16 @@ struct Work {
     int pad;
 };
 
+// One tensor-core work item: 128 pairs x N field rows (N = 8 nbox rounded up to 16).
+struct TcWork {
+    int pair0, npairs;      // pairs [pair0, pair0 + npairs), npairs <= 128
+    int shell_lo, nshell;   // F0 rows the pairs use, nshell <= 64
+    int nbox;               // boxes of 8 consecutive field rows
+    int n;                  // MMA N
+    int pad[2];
+    int box_field[16];      // first field row of each box
+};
+
 struct BinLoc {   // where T of (l, bin) lives in the partial buffer
     int work;
     int row;      // row within the work item
@@ -68,6 +80,7 @@ template <typename R>
 cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const int16_t* shell_of,
                               const float* radial, const FieldDesc* d_fields, int nfields,
                               const cx<R>* tw, cx<R>* t1, cx<R>* t2, R* out, size_t out_stride,
+                              uint32_t* hi, uint32_t* lo, int f16, unsigned* fmax2, unsigned* f0max,
                               cudaStream_t st);
 
 // ---- launchers (bsp_contract.cu) ----
@@ -76,8 +89,15 @@ cudaError_t launch_contract_cc(const R* fields, size_t fstride, const Work* work
                                const int2* pair_fields, const int* row_fields, size_t npts,
                                int nsplit, double* partial, cudaStream_t st);
 
-cudaError_t launch_reduce(const double* partial, int nsplit, const BinLoc* loc, int nout,
-                          int nbins, const double* counts, double scale, int mode, double* T_out,
-                          double* out, cudaStream_t st);
+cudaError_t launch_reduce(const double* partial, int nsplit, size_t unit, int row_stride,
+                          const BinLoc* loc, int nout, int nbins, const double* counts, double scale,
+                          int mode, double* T_out, double* out, cudaStream_t st);
+
+// ---- launchers (bsp_tc.cu) ----
+size_t tc_smem_bytes();
+cudaError_t launch_contract_tc(bool f16, const void* tm_f0, const void* tm_hi, const void* tm_lo,
+                               const TcWork* works, int nwork, const int2* pair_shells,
+                               const unsigned* f0max, const unsigned* fmax2, float bound_mul, size_t npts,
+                               int nsplit, int nprod, int chunk_kb, double* partial, int* err, cudaStream_t st);
 
 }  // namespace bsp

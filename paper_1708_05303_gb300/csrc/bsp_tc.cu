@@ -1,0 +1,451 @@
+// bsp_tc.cu -- tensor-core (tcgen05) contraction of the filtered fields.
+//
+// The x-integral of Eq. Standard_ell_Estim (Sec. 3.1),
+//   T^l[a; b, c] = sum_x F^l_a(x) F^0_b(x) F^0_c(x),
+// is a dense contraction over x once the pair products P_bc = F^0_b F^0_c
+// are formed: D[pair][row] = sum_x P_pair(x) F_row(x), rows = fields (l, a).
+// A CTA owns one tile -- 128 pairs (the MMA M) times N <= 128 field rows --
+// and one x-segment, and runs a warp-specialised pipeline per K-block of 64
+// points:
+//   warp 0      TMA: F^0 rows (FP32) for the pairs, and the 16-bit hi/lo
+//               planes of the tile's field rows (128-byte swizzled boxes);
+//   warps 4-11  form P = F_b F_c in FP32, split it into 16-bit hi + lo,
+//               and store both in the K-major 128-byte-swizzled layout the
+//               MMA reads;
+//   warp 1      one thread issues tcgen05.mma kind::f16, M=128, K=16:
+//               D += P_hi F_hi + P_hi F_lo + P_lo F_hi (split products;
+//               one product for the plain 16-bit mode), FP32 accumulators
+//               in tensor memory;
+//   warps 12-15 drain the accumulator every `chunk` K-blocks (tcgen05.ld) and
+//               fold it into compensated FP32 (TwoSum hi + lo) running sums
+//               kept in tensor memory, written once to FP64 at the end.
+// Two smem stages and two accumulator buffers keep TMA, the CUDA-core
+// prologue, the MMAs and the epilogue overlapped.  Every mbarrier wait is
+// bounded; on timeout the CTA records an error code, stops, waits (bounded)
+// for its own copies in flight and releases its tensor memory.
+#include <cuda.h>
+
+#include "bsp_internal.h"
+
+namespace bsp {
+
+namespace {
+
+constexpr int TC_M = 128;        // pairs per tile = MMA M
+constexpr int TC_NMAX = 128;     // field rows per tile = MMA N (max)
+constexpr int TC_KB = 64;        // x-points per K-block (128 bytes of 16-bit values)
+constexpr int TC_STAGES = 2;
+constexpr int TC_MAXSH = 64;     // F0 rows per tile
+constexpr int TC_THREADS = 512;  // 16 warps
+constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, N_PRO = 8, W_EPI0 = 12;
+constexpr uint32_t TMEM_COLS = 512;   // acc0 [0,128) acc1 [128,256) hi [256,384) lo [384,512)
+constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
+
+struct TcSmem {
+    uint8_t a_hi[TC_STAGES][TC_M * 128];
+    uint8_t a_lo[TC_STAGES][TC_M * 128];
+    uint8_t b_hi[TC_STAGES][TC_NMAX * 128];
+    uint8_t b_lo[TC_STAGES][TC_NMAX * 128];
+    float f0[TC_STAGES][TC_MAXSH * TC_KB];
+    uint64_t full_tma[TC_STAGES], full_a[TC_STAGES], empty[TC_STAGES], acc_full[2], acc_empty[2];
+    uint32_t tmem_base;
+    volatile int abort;
+    int2 pf[TC_M];
+    float pscale[TC_M];
+    float fscale[TC_NMAX];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// Wait for the phase of parity `parity` to complete; false after ~4 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    const uint32_t addr = smem_u32(b);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand in 8-row x 128-byte atoms
+// with the 128-byte swizzle, atoms 1024 bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address >> 4
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset >> 4
+    d |= (uint64_t)1 << 46;                     // descriptor version (0b001)
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, A and B of the same
+// 16-bit type (0 = FP16, 1 = BF16), both K-major, M = 128.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t n) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+// Two FP32 values -> packed 16-bit pair (x0 in the low half), round to nearest even.
+template <bool F16>
+__device__ __forceinline__ uint32_t pack2(float x0, float x1) {
+    uint32_t r;
+    if (F16) asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+    else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+    return r;
+}
+template <bool F16>
+__device__ __forceinline__ void unpack2(uint32_t v, float& x0, float& x1) {
+    if (F16) {
+        unsigned short l = (unsigned short)(v & 0xFFFFu), h = (unsigned short)(v >> 16);
+        asm("cvt.f32.f16 %0, %1;" : "=f"(x0) : "h"(l));
+        asm("cvt.f32.f16 %0, %1;" : "=f"(x1) : "h"(h));
+    } else {
+        x0 = __uint_as_float(v << 16);
+        x1 = __uint_as_float(v & 0xFFFF0000u);
+    }
+}
+
+// Power of two s with bound * s in [2^14, 2^15) (see the FFT's pass 3).
+__device__ __forceinline__ float pow2_scale(float bound) {
+    if (!(bound > 0.f)) return 1.f;
+    int e;
+    frexpf(bound, &e);
+    return ldexpf(1.f, 15 - e);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void set_abort(TcSmem& S, int* err, int code) {
+    S.abort = 1;
+    atomicOr(err, code);
+}
+
+template <bool F16>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_contract_tc(const __grid_constant__ CUtensorMap tm_f0, const __grid_constant__ CUtensorMap tm_hi,
+                  const __grid_constant__ CUtensorMap tm_lo, const TcWork* __restrict__ works,
+                  const int2* __restrict__ pair_shells, const unsigned* __restrict__ f0max,
+                  const unsigned* __restrict__ fmax2, float bound_mul, int nkb_total, int kb_per_split, int nprod,
+                  int CHUNK, double* __restrict__ partial, int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const TcWork w = works[blockIdx.x];
+    const int kb0 = blockIdx.y * kb_per_split;
+    const int nkb = max(0, min(nkb_total, kb0 + kb_per_split) - kb0);
+    const int nch = (nkb + CHUNK - 1) / CHUNK;
+    const uint32_t N = (uint32_t)w.n;
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&S.full_tma[s], 1);
+            mbar_init(&S.full_a[s], N_PRO);
+            mbar_init(&S.empty[s], 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(&S.acc_full[j], 1);
+            mbar_init(&S.acc_empty[j], 4);
+        }
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < TC_M) {
+        int2 v = {-1, -1};
+        float sc = 1.f;
+        if (tid < w.npairs) {
+            v = pair_shells[w.pair0 + tid];
+            // exact max |F_b| |F_c| bounds the pair product: scale it below 2^15
+            sc = pow2_scale(__uint_as_float(f0max[v.x]) * __uint_as_float(f0max[v.y]));
+            v.x -= w.shell_lo;
+            v.y -= w.shell_lo;
+        }
+        S.pf[tid] = v;
+        S.pscale[tid] = sc;
+    } else if (tid < TC_M + TC_NMAX) {
+        // the scale the FFT applied to this field row's 16-bit planes
+        const int c = tid - TC_M;
+        float fs = 1.f;
+        if (c < 8 * w.nbox) fs = pow2_scale(bound_mul * __uint_as_float(fmax2[w.box_field[c >> 3] + (c & 7)]));
+        S.fscale[c] = fs;
+    }
+    if (warp == W_MMA) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&S.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == W_TMA) {
+        if (lane == 0) {
+            const int nfb = (w.nshell + 7) >> 3;
+            const int nbb = (int)N >> 3;   // boxes including the padding box
+            const uint32_t bytes = (uint32_t)nfb * 8 * TC_KB * 4 + (uint32_t)nbb * 1024 * 2;
+            int last_use[TC_STAGES] = {-1, -1};
+            for (int k = 0; k < nkb && !S.abort; ++k) {
+                const int s = k & 1, use = k >> 1;
+                if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1)) {
+                    set_abort(S, err, 1);
+                    break;
+                }
+                mbar_expect_tx(&S.full_tma[s], bytes);
+                const int x0 = (kb0 + k) * TC_KB;
+                for (int j = 0; j < nfb; ++j)
+                    tma_load_2d(&S.f0[s][j * 8 * TC_KB], &tm_f0, x0, w.shell_lo + 8 * j, &S.full_tma[s]);
+                for (int j = 0; j < nbb; ++j) {
+                    const int f = w.box_field[j < w.nbox ? j : w.nbox - 1];
+                    tma_load_2d(&S.b_hi[s][j * 1024], &tm_hi, x0, f, &S.full_tma[s]);
+                    tma_load_2d(&S.b_lo[s][j * 1024], &tm_lo, x0, f, &S.full_tma[s]);
+                }
+                last_use[s] = use;
+            }
+            // copies in flight must land before the CTA can exit
+            for (int s = 0; s < TC_STAGES; ++s)
+                if (last_use[s] >= 0 && !mbar_wait(&S.full_tma[s], last_use[s] & 1)) atomicOr(err, 16);
+        }
+    } else if (warp == W_MMA) {
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(F16 ? 0u : 1u, N);
+            int last_s = -1, last_use = 0;
+            for (int k = 0; k < nkb && !S.abort; ++k) {
+                const int s = k & 1, use = k >> 1;
+                const int c = k / CHUNK, j = c & 1;
+                const bool first = (k % CHUNK) == 0;
+                const bool last = (k % CHUNK) == CHUNK - 1 || k == nkb - 1;
+                if (first && c >= 2 && !mbar_wait(&S.acc_empty[j], ((c >> 1) - 1) & 1)) {
+                    set_abort(S, err, 2);
+                    break;
+                }
+                if (!mbar_wait(&S.full_tma[s], use & 1) || !mbar_wait(&S.full_a[s], use & 1)) {
+                    set_abort(S, err, 4);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(j * 128);
+                const uint32_t ah = smem_u32(S.a_hi[s]), al = smem_u32(S.a_lo[s]);
+                const uint32_t bh = smem_u32(S.b_hi[s]), bl = smem_u32(S.b_lo[s]);
+#pragma unroll
+                for (int kk = 0; kk < TC_KB / 16; ++kk) {
+                    const uint32_t o = (uint32_t)kk * 32;
+                    mma_16(d, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (first && kk == 0) ? 0u : 1u);
+                    if (nprod == 3) {
+                        mma_16(d, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1u);
+                        mma_16(d, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1u);
+                    }
+                }
+                mma_commit(&S.empty[s]);
+                if (last) mma_commit(&S.acc_full[j]);
+                last_s = s;
+                last_use = use;
+            }
+            // the last MMAs must finish before tensor memory is released
+            if (last_s >= 0 && !mbar_wait(&S.empty[last_s], last_use & 1)) atomicOr(err, 32);
+        }
+    } else if (warp >= W_PRO0 && warp < W_PRO0 + N_PRO) {
+        const int wr = warp - W_PRO0;
+        for (int k = 0; k < nkb && !S.abort; ++k) {
+            const int s = k & 1, use = k >> 1;
+            if (!mbar_wait(&S.full_tma[s], use & 1)) {
+                set_abort(S, err, 8);
+                break;
+            }
+            const float* f0 = S.f0[s];
+            uint8_t* ah = S.a_hi[s];
+            uint8_t* al = S.a_lo[s];
+#pragma unroll 4
+            for (int r = 0; r < TC_M / N_PRO; ++r) {
+                const int i = wr * (TC_M / N_PRO) + r;
+                const int2 bc = S.pf[i];
+                float p0 = 0.f, p1 = 0.f;
+                if (bc.x >= 0) {
+                    const float2 fb = *reinterpret_cast<const float2*>(&f0[bc.x * TC_KB + 2 * lane]);
+                    const float2 fc = *reinterpret_cast<const float2*>(&f0[bc.y * TC_KB + 2 * lane]);
+                    const float sc = S.pscale[i];
+                    p0 = fb.x * fc.x * sc;
+                    p1 = fb.y * fc.y * sc;
+                }
+                const uint32_t hi = pack2<F16>(p0, p1);
+                float h0, h1;
+                unpack2<F16>(hi, h0, h1);
+                const uint32_t lo = pack2<F16>(p0 - h0, p1 - h1);
+                // element (i, k = 2 lane): 16-byte chunk lane/4, swizzled by row i mod 8
+                const int off = (i >> 3) * 1024 + (i & 7) * 128 + (((lane >> 2) ^ (i & 7)) << 4) + ((lane & 3) << 2);
+                *reinterpret_cast<uint32_t*>(ah + off) = hi;
+                *reinterpret_cast<uint32_t*>(al + off) = lo;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.full_a[s]);
+        }
+    } else if (warp >= W_EPI0) {
+        const int q = warp & 3;
+        const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
+        for (int c = 0; c < nch && !S.abort; ++c) {
+            const int j = c & 1;
+            if (!mbar_wait(&S.acc_full[j], (c >> 1) & 1)) {
+                set_abort(S, err, 64);
+                break;
+            }
+            tc_fence_after();
+            for (uint32_t col = 0; col < N; col += 16) {
+                uint32_t a[16], h[16], l[16];
+                tmem_ld16(lanebase + (uint32_t)(j * 128) + col, a);
+                if (c > 0) {
+                    tmem_ld16(lanebase + 256 + col, h);
+                    tmem_ld16(lanebase + 384 + col, l);
+                }
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (c == 0) {
+                        h[i] = a[i];
+                        l[i] = 0u;
+                    } else {
+                        float s, e;
+                        two_sum(__uint_as_float(h[i]), __uint_as_float(a[i]), s, e);
+                        h[i] = __float_as_uint(s);
+                        l[i] = __float_as_uint(__uint_as_float(l[i]) + e);
+                    }
+                }
+                tmem_st16(lanebase + 256 + col, h);
+                tmem_st16(lanebase + 384 + col, l);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.acc_empty[j]);
+        }
+        // final: hi + lo in FP64, unscaled, to this CTA's partial slot
+        const int row = 32 * q + lane;
+        double* dst = partial + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (TC_M * TC_NMAX) +
+                      (size_t)row * TC_NMAX;
+        const bool have = nch > 0 && !S.abort;
+        if (have) tc_fence_after();
+        for (uint32_t col = 0; col < N; col += 16) {
+            uint32_t h[16], l[16];
+            if (have) {
+                tmem_ld16(lanebase + 256 + col, h);
+                tmem_ld16(lanebase + 384 + col, l);
+                tmem_ld_wait();
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                double v = have ? (double)__uint_as_float(h[i]) + (double)__uint_as_float(l[i]) : 0.0;
+                v /= (double)S.pscale[row] * (double)S.fscale[col + i];
+                dst[col + i] = v;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == W_MMA) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
+
+cudaError_t launch_contract_tc(bool f16, const void* tm_f0, const void* tm_hi, const void* tm_lo,
+                               const TcWork* works, int nwork, const int2* pair_shells, const unsigned* f0max,
+                               const unsigned* fmax2, float bound_mul, size_t npts, int nsplit, int nprod,
+                               int chunk_kb, double* partial, int* err, cudaStream_t st) {
+    const int nkb_total = (int)((npts + TC_KB - 1) / TC_KB);
+    const int kb_per_split = (nkb_total + nsplit - 1) / nsplit;
+    const size_t smem = tc_smem_bytes();
+    const CUtensorMap& a = *reinterpret_cast<const CUtensorMap*>(tm_f0);
+    const CUtensorMap& b = *reinterpret_cast<const CUtensorMap*>(tm_hi);
+    const CUtensorMap& c = *reinterpret_cast<const CUtensorMap*>(tm_lo);
+    dim3 grid(nwork, nsplit);
+    cudaError_t e;
+    if (f16) {
+        if ((e = cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        k_contract_tc<true><<<grid, TC_THREADS, smem, st>>>(a, b, c, works, pair_shells, f0max, fmax2, bound_mul,
+                                                            nkb_total, kb_per_split, nprod, chunk_kb, partial, err);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        k_contract_tc<false><<<grid, TC_THREADS, smem, st>>>(a, b, c, works, pair_shells, f0max, fmax2,
+                                                             bound_mul, nkb_total, kb_per_split, nprod, chunk_kb,
+                                                             partial, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace bsp

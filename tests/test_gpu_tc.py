@@ -1,0 +1,92 @@
+"""GPU parity of the tensor-core (tcgen05) contraction against the FP64 oracle.
+
+split_f16: power-of-two scaled FP16 hi + lo split of both operands (22
+significant bits), three products, FP32 accumulation: gated at 1e-5 of
+max(|B|, rms_l) like the FP32 path.
+split_bf16: the BF16 hi + lo split (16 significant bits; its representation
+error alone is ~5e-5 of the gate scale on small grids, computed exactly on
+the CPU for the same inputs), gated at 2e-4 and reported.
+bf16: one product; its error is reported and only bounded loosely.
+Every run also checks the kernels' device error word.
+"""
+import numpy as np
+import pytest
+
+from paper_1708_05303_gb300.synth import FieldModel, linear_edges, make_field
+
+pytestmark = pytest.mark.gpu
+BOX = 1000.0
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_05303_gb300 import build
+
+    build.build()
+    return torch
+
+
+def gate(B_gpu, B_ora):
+    rms = np.sqrt(np.mean(B_ora ** 2, axis=1, keepdims=True))
+    return np.max(np.abs(B_gpu - B_ora) / np.maximum(np.abs(B_ora), rms))
+
+
+def run(torch, dk, n, edges, ells, prec):
+    from paper_1708_05303_gb300 import bsp
+
+    est = bsp.Bispectrum(n, BOX, edges, ells, prec=prec)
+    B = est.compute(torch.from_numpy(np.ascontiguousarray(dk)).cuda()).cpu().numpy()
+    torch.cuda.synchronize()
+    status = bsp.bsp_device_status(est.plan)
+    bins = est.bins.copy()
+    est.close()
+    return bins, B, status
+
+
+CASES = [
+    (16, [1, 3, 5, 7], (0, 2, 4), 1),
+    (32, linear_edges(8), (0, 2, 4), 5),
+    (24, [1, 3, 5, 7, 9, 11], (0, 2), 3),
+    (64, linear_edges(16), (0, 2, 4), 1709),
+]
+
+
+GATES = {"split_f16": 1e-5, "split_bf16": 2e-4}
+
+
+@pytest.mark.parametrize("prec", ["split_f16", "split_bf16"])
+@pytest.mark.parametrize("n,edges,ells,seed", CASES)
+def test_split_matches_oracle(torch_cuda, ora, n, edges, ells, seed, prec):
+    model = FieldModel(n=n, box=BOX, sigma_g=0.3 if seed != 1709 else None)
+    dk, _ = make_field(model, seed)
+    bins, B, status = run(torch_cuda, dk, n, edges, ells, prec)
+    assert status == 0
+    r = ora.bispectrum(dk.astype(np.complex128), n, BOX, edges, ells)
+    assert np.array_equal(bins, r["bins"])
+    err = gate(B, r["B"])
+    print("%s n=%d gate error %.3g" % (prec, n, err))
+    assert err <= GATES[prec], err
+
+
+@pytest.mark.parametrize("n,edges,ells,seed", CASES[:2])
+def test_plain_bf16_is_bounded(torch_cuda, ora, n, edges, ells, seed):
+    dk, _ = make_field(FieldModel(n=n, box=BOX, sigma_g=0.3), seed)
+    bins, B, status = run(torch_cuda, dk, n, edges, ells, "bf16")
+    assert status == 0
+    r = ora.bispectrum(dk.astype(np.complex128), n, BOX, edges, ells)
+    err = gate(B, r["B"])
+    print("bf16 n=%d gate error %.3g" % (n, err))
+    assert err < 0.1
+
+
+def test_split_f16_close_to_fp32_path(torch_cuda):
+    n = 48
+    edges = linear_edges(10)
+    dk, _ = make_field(FieldModel(n=n, box=BOX, sigma_g=0.3), 6)
+    _, B32, _ = run(torch_cuda, dk, n, edges, (0, 2, 4), "fp32")
+    _, Btc, status = run(torch_cuda, dk, n, edges, (0, 2, 4), "split_f16")
+    assert status == 0
+    assert gate(Btc, B32) <= 2e-5
