@@ -112,6 +112,14 @@ bsp_status bsp_workspace_size(const bsp_plan* plan, size_t* bytes);
 bsp_status bsp_counts(bsp_plan* plan, void* ws, void* stream);
 
 /*
+ * Copy the counts and valid bins of `src` (after its bsp_counts) into `dst`,
+ * a plan of the same grid and shells (any multipoles or precision), instead
+ * of counting again.  Host-side plus small uploads; BSP_EINVAL if the
+ * geometries differ, BSP_ESTATE if src has no counts.
+ */
+bsp_status bsp_plan_share_counts(bsp_plan* dst, const bsp_plan* src);
+
+/*
  * The valid bins after bsp_counts: *n_bins always; if abc != NULL the
  * bins as int32 [n_bins][3] (a, b, c); if counts != NULL the FP64 counts
  * [n_bins].  BSP_ESTATE before bsp_counts.
@@ -180,6 +188,7 @@ bsp_status bsp_device_status(bsp_plan* plan, int* code);
  */
 bsp_status bsp_set_profiling(bsp_plan* plan, int on);
 bsp_status bsp_phase_times(bsp_plan* plan, double* ms, int* ncalls, int* launches);
+
 
 /* Human-readable text for a status, and the last CUDA error text seen by
  * this thread ("" if none). */

@@ -32,6 +32,7 @@ _SIGS = [
     ("bsp_host_staging_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("bsp_counts", ctypes.c_int, [_P, _P, _P]),
     ("bsp_plan_bins", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P, _P]),
+    ("bsp_plan_share_counts", ctypes.c_int, [_P, _P]),
     ("bsp_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_compute_host", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_last_raw", ctypes.c_int, [_P, _P, _P, _P]),
@@ -128,6 +129,10 @@ def bsp_counts(plan: int, ws, stream=None):
     _check(load().bsp_counts(plan, _dptr(ws), _stream_handle(stream)), "bsp_counts")
 
 
+def bsp_plan_share_counts(dst: int, src: int):
+    _check(load().bsp_plan_share_counts(dst, src), "bsp_plan_share_counts")
+
+
 def bsp_plan_bins(plan: int):
     lib = load()
     nb = ctypes.c_int()
@@ -197,7 +202,8 @@ class Bispectrum:
     construction.  ``compute(delta_k)`` returns B [n_ell][n_bins] (FP64,
     device) for a complex64 [n][n][n/2+1] CUDA tensor."""
 
-    def __init__(self, n, box, edges, ells=(0, 2, 4), prec="fp32", host_staging=False, stream=None):
+    def __init__(self, n, box, edges, ells=(0, 2, 4), prec="fp32", host_staging=False, stream=None,
+                 counts_from=None, ws=None):
         import torch
 
         self.n, self.box, self.ells = int(n), float(box), tuple(ells)
@@ -205,8 +211,14 @@ class Bispectrum:
         nbytes = bsp_workspace_size(self.plan)
         if host_staging:
             nbytes += bsp_host_staging_size(self.plan)
-        self.ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
-        bsp_counts(self.plan, self.ws, stream)
+        if ws is not None and ws.numel() >= nbytes:
+            self.ws = ws
+        else:
+            self.ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+        if counts_from is not None:
+            bsp_plan_share_counts(self.plan, counts_from.plan)
+        else:
+            bsp_counts(self.plan, self.ws, stream)
         self.bins, self.counts = bsp_plan_bins(self.plan)
         self.B = torch.empty((len(self.ells), len(self.bins)), dtype=torch.float64, device="cuda")
 

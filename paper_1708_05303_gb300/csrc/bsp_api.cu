@@ -577,6 +577,31 @@ bsp_status bsp_host_staging_size(const bsp_plan* p, size_t* bytes) {
     return BSP_OK;
 }
 
+// After the valid bins and counts are known: contraction schedules and the
+// device copy of the counts.
+static bsp_status finish_counts(bsp_plan* p) {
+    p->comp_sched = build_sched(p->bins, p->out_slots, p->nsh, p->npts(), p->target_ctas, CCOLS);
+    if (round256(partial_bytes(p->comp_sched, CCOLS)) > p->part_bytes) return BSP_ENOMEM;
+    bsp_status s = upload_sched(p->comp_dev, p->comp_sched);
+    if (s != BSP_OK) return s;
+    if (p->tc) {
+        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->nsh, p->npts());
+        if (round256(p->tc_sched.works.size() * (size_t)p->tc_sched.nsplit * TC_UNIT * sizeof(double)) >
+            p->tc_part_bytes)
+            return BSP_ENOMEM;
+        cudaFree(p->d_tc_works); cudaFree(p->d_tc_pairs); cudaFree(p->d_tc_loc);
+        p->d_tc_works = nullptr; p->d_tc_pairs = nullptr; p->d_tc_loc = nullptr;
+        if ((s = upload(&p->d_tc_works, p->tc_sched.works)) != BSP_OK) return s;
+        if ((s = upload(&p->d_tc_pairs, p->tc_sched.pairs)) != BSP_OK) return s;
+        if ((s = upload(&p->d_tc_loc, p->tc_sched.loc)) != BSP_OK) return s;
+    }
+    cudaFree(p->d_counts);
+    p->d_counts = nullptr;
+    if ((s = upload(&p->d_counts, p->counts)) != BSP_OK) return s;
+    p->have_counts = true;
+    return BSP_OK;
+}
+
 bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
     if (!p || !ws || !aligned256(ws)) return BSP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -615,26 +640,16 @@ bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
             p->bins.push_back(p->cand[i]);
             p->counts.push_back(hc[i]);
         }
-    p->comp_sched = build_sched(p->bins, p->out_slots, p->nsh, p->npts(), p->target_ctas, CCOLS);
-    if (round256(partial_bytes(p->comp_sched, CCOLS)) > p->part_bytes) return BSP_ENOMEM;
-    bsp_status s = upload_sched(p->comp_dev, p->comp_sched);
-    if (s != BSP_OK) return s;
-    if (p->tc) {
-        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->nsh, p->npts());
-        if (round256(p->tc_sched.works.size() * (size_t)p->tc_sched.nsplit * TC_UNIT * sizeof(double)) >
-            p->tc_part_bytes)
-            return BSP_ENOMEM;
-        cudaFree(p->d_tc_works); cudaFree(p->d_tc_pairs); cudaFree(p->d_tc_loc);
-        p->d_tc_works = nullptr; p->d_tc_pairs = nullptr; p->d_tc_loc = nullptr;
-        if ((s = upload(&p->d_tc_works, p->tc_sched.works)) != BSP_OK) return s;
-        if ((s = upload(&p->d_tc_pairs, p->tc_sched.pairs)) != BSP_OK) return s;
-        if ((s = upload(&p->d_tc_loc, p->tc_sched.loc)) != BSP_OK) return s;
-    }
-    cudaFree(p->d_counts);
-    p->d_counts = nullptr;
-    if ((s = upload(&p->d_counts, p->counts)) != BSP_OK) return s;
-    p->have_counts = true;
-    return BSP_OK;
+    return finish_counts(p);
+}
+
+bsp_status bsp_plan_share_counts(bsp_plan* dst, const bsp_plan* src) {
+    if (!dst || !src || dst == src) return BSP_EINVAL;
+    if (!src->have_counts) return BSP_ESTATE;
+    if (dst->n != src->n || dst->nsh != src->nsh || dst->edges != src->edges) return BSP_EINVAL;
+    dst->bins = src->bins;
+    dst->counts = src->counts;
+    return finish_counts(dst);
 }
 
 bsp_status bsp_plan_bins(const bsp_plan* p, int* n_bins, int32_t* abc, double* counts) {

@@ -99,55 +99,100 @@ __device__ __forceinline__ void butterfly(cx<R>* v) {
     }
 }
 
+// Shared-memory layouts of P pencils of length M (one element = one complex):
+//   pencil-fast (passes 1, 2):  (p, i) -> i P + p + i/8
+//   index-fast  (pass 3):       (p, i) -> p PS + i + i/8,  PS = M + M/8 + 1
+// The i/8 padding spreads the strided Stockham accesses over all banks.
+template <bool PF, int P>
+__device__ __forceinline__ int sidx(int p, int i, int M) {
+    return PF ? i * P + p + (i >> 3) : p * (M + (M >> 3) + 1) + i + (i >> 3);
+}
+template <bool PF, int P>
+__host__ __device__ constexpr int smem_elems(int M) {
+    return PF ? M * P + (M >> 3) + 1 : P * (M + (M >> 3) + 1);
+}
+
 // One Stockham stage of radix RADIX over P pencils of length M, out of
-// place from src to dst in shared memory; element (pencil p, index i) lives
-// at buf[p*ps + i*is].  Butterfly j reads x[j + r M/RADIX], twiddles by
+// place from src to dst.  Butterfly j reads x[j + r M/RADIX], twiddles by
 // W_M^{r (j mod Ns) M/(Ns RADIX)} and writes y[(j/Ns) Ns RADIX + j mod Ns + r Ns]
-// (autosort: natural order after the last stage).
-template <typename R, int RADIX, bool pfast>
-__device__ __forceinline__ void fft_stage(const cx<R>* __restrict__ src, cx<R>* __restrict__ dst, int M,
-                                          int Ns, int P, int ps, int is, const cx<R>* tw, int twmul) {
+// (autosort: natural order after the last stage).  With M and Ns compile-time
+// constants (the specialised kernels) all index arithmetic folds to shifts.
+template <typename R, int RADIX, bool PF, int P>
+__device__ __forceinline__ void fft_stage(const cx<R>* __restrict__ src, cx<R>* __restrict__ dst, int M, int Ns,
+                                          const cx<R>* tw, int twmul) {
     const int nbf = M / RADIX;
     const int total = nbf * P;
     for (int b = threadIdx.x; b < total; b += NTHR) {
         int p, j;
-        if (pfast) { p = b % P; j = b / P; } else { j = b % nbf; p = b / nbf; }
+        if (PF) { p = b % P; j = b / P; } else { j = b % nbf; p = b / nbf; }
         const int k = j % Ns;
         const int tstep = k * (M / (Ns * RADIX)) * twmul;
-        const cx<R>* in = src + p * ps;
         cx<R> v[RADIX];
 #pragma unroll
         for (int r = 0; r < RADIX; ++r) {
-            cx<R> x = in[(j + r * nbf) * is];
+            const cx<R> x = src[sidx<PF, P>(p, j + r * nbf, M)];
             v[r] = r == 0 ? x : cmul(x, tw[r * tstep]);
         }
         butterfly<R, RADIX>(v);
-        cx<R>* out = dst + p * ps;
         const int o = (j / Ns) * Ns * RADIX + k;
 #pragma unroll
-        for (int r = 0; r < RADIX; ++r) out[(o + r * Ns) * is] = v[r];
+        for (int r = 0; r < RADIX; ++r) dst[sidx<PF, P>(p, o + r * Ns, M)] = v[r];
     }
     __syncthreads();
 }
 
-// Inverse DFT of P pencils held in a; b is scratch of the same shape.
-// Returns the buffer that holds the result.
-template <typename R, bool pfast>
-__device__ cx<R>* fft_pingpong(cx<R>* a, cx<R>* b, int M, int P, int ps, int is, const int* rad, int nrad,
-                               const cx<R>* tw, int twmul) {
+// Runtime radix list (any supported length).  Returns the result buffer.
+template <typename R, bool PF, int P>
+__device__ cx<R>* fft_pingpong(cx<R>* a, cx<R>* b, int M, const int* rad, int nrad, const cx<R>* tw, int twmul) {
     int Ns = 1;
     for (int s = 0; s < nrad; ++s) {
         switch (rad[s]) {
-            case 8: fft_stage<R, 8, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
-            case 4: fft_stage<R, 4, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
-            case 2: fft_stage<R, 2, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
-            case 3: fft_stage<R, 3, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
-            case 5: fft_stage<R, 5, pfast>(a, b, M, Ns, P, ps, is, tw, twmul); break;
+            case 8: fft_stage<R, 8, PF, P>(a, b, M, Ns, tw, twmul); break;
+            case 4: fft_stage<R, 4, PF, P>(a, b, M, Ns, tw, twmul); break;
+            case 2: fft_stage<R, 2, PF, P>(a, b, M, Ns, tw, twmul); break;
+            case 3: fft_stage<R, 3, PF, P>(a, b, M, Ns, tw, twmul); break;
+            case 5: fft_stage<R, 5, PF, P>(a, b, M, Ns, tw, twmul); break;
         }
         Ns *= rad[s];
         cx<R>* t = a; a = b; b = t;
     }
     return a;
+}
+
+// Compile-time radix list: 8s first, then 4 / 4x4 / 2 for the leftover
+// power of two, then 3s and 5s (the host's plan for the runtime path is the same).
+struct RadixList {
+    int n;
+    int r[8];
+};
+__host__ __device__ constexpr RadixList radix_list(int m) {
+    RadixList L{0, {0, 0, 0, 0, 0, 0, 0, 0}};
+    int a = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    int n8 = a / 3, rem = a % 3;
+    int n44 = 0, n2 = 0, n4 = 0;
+    if (rem == 1 && n8 > 0) { --n8; n44 = 1; }
+    else if (rem == 1) n2 = 1;
+    else if (rem == 2) n4 = 1;
+    for (int i = 0; i < n8; ++i) L.r[L.n++] = 8;
+    if (n44) { L.r[L.n++] = 4; L.r[L.n++] = 4; }
+    if (n2) L.r[L.n++] = 2;
+    if (n4) L.r[L.n++] = 4;
+    while (m % 3 == 0) { m /= 3; L.r[L.n++] = 3; }
+    while (m % 5 == 0) { m /= 5; L.r[L.n++] = 5; }
+    return L;
+}
+
+template <typename R, bool PF, int P, int M, int S = 0, int NS = 1>
+__device__ __forceinline__ cx<R>* fft_ct(cx<R>* a, cx<R>* b, const cx<R>* tw, int twmul) {
+    constexpr RadixList L = radix_list(M);
+    if constexpr (S >= L.n) {
+        return a;
+    } else {
+        constexpr int RADIX = L.r[S];
+        fft_stage<R, RADIX, PF, P>(a, b, M, NS, tw, twmul);
+        return fft_ct<R, PF, P, M, S + 1, NS * RADIX>(b, a, tw, twmul);
+    }
 }
 
 __device__ __forceinline__ int freq_of(int idx, int n) { return idx < n / 2 ? idx : idx - n; }
@@ -167,7 +212,7 @@ __device__ __forceinline__ R filter_weight(const FieldDesc& fd, int n2, int fz, 
 }
 
 // Pass 1: filter + inverse DFT along x for P consecutive f_z of one f_y.
-template <typename R, int P>
+template <typename R, int P, int NN>
 __global__ void __launch_bounds__(NTHR) k_pass1(FftGeom g, const cx<float>* __restrict__ delta,
                                                 const int16_t* __restrict__ shell_of,
                                                 const float* __restrict__ radial,
@@ -175,10 +220,10 @@ __global__ void __launch_bounds__(NTHR) k_pass1(FftGeom g, const cx<float>* __re
                                                 const cx<R>* __restrict__ twg, cx<R>* __restrict__ t1,
                                                 size_t t1_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = NN ? NN : g.n;
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
-    cx<R>* buf = tw + g.n;
-    cx<R>* scr = buf + g.n * P;
-    const int N = g.n;
+    cx<R>* buf = tw + N;
+    cx<R>* scr = buf + smem_elems<true, P>(N);
     const FieldDesc fd = fields[blockIdx.y];
     const int nkzb = (g.nKz + P - 1) / P;
     const int cy = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P;
@@ -207,14 +252,16 @@ __global__ void __launch_bounds__(NTHR) k_pass1(FftGeom g, const cx<float>* __re
                 }
             }
         }
-        buf[ix * P + p] = val;
+        buf[sidx<true, P>(p, ix, N)] = val;
     }
     __syncthreads();
-    const cx<R>* res = fft_pingpong<R, true>(buf, scr, N, P, 1, P, g.rad, g.nrad, tw, 1);
+    const cx<R>* res;
+    if constexpr (NN > 0) res = fft_ct<R, true, P, NN>(buf, scr, tw, 1);
+    else res = fft_pingpong<R, true, P>(buf, scr, N, g.rad, g.nrad, tw, 1);
     cx<R>* dst = t1 + (size_t)blockIdx.y * t1_stride;
     for (int e = threadIdx.x; e < N * P; e += NTHR) {
         const int p = e % P, x = e / P, kz = kz0 + p;
-        if (kz < g.nKz) dst[((size_t)cy * N + x) * g.nKz + kz] = res[x * P + p];
+        if (kz < g.nKz) dst[((size_t)cy * N + x) * g.nKz + kz] = res[sidx<true, P>(p, x, N)];
     }
 }
 
@@ -234,16 +281,16 @@ __device__ __forceinline__ float pow2_scale(float bound) {
     return ldexpf(1.f, 15 - e);
 }
 
-template <typename R, int P>
+template <typename R, int P, int NN>
 __global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restrict__ t1,
                                                 size_t t1_stride, const cx<R>* __restrict__ twg,
                                                 cx<R>* __restrict__ t2, size_t t2_stride,
                                                 const FieldDesc* __restrict__ fields, unsigned* __restrict__ fmax2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = NN ? NN : g.n;
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
-    cx<R>* buf = tw + g.n;
-    cx<R>* scr = buf + g.n * P;
-    const int N = g.n;
+    cx<R>* buf = tw + N;
+    cx<R>* scr = buf + smem_elems<true, P>(N);
     const int nkzb = (g.nKz + P - 1) / P;
     const int x = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P;
     const cx<R>* src = t1 + (size_t)blockIdx.y * t1_stride;
@@ -256,16 +303,18 @@ __global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restri
             const int cy = g.pruned ? fy + g.K : iy;
             val = src[((size_t)cy * N + x) * g.nKz + kz];
         }
-        buf[iy * P + p] = val;
+        buf[sidx<true, P>(p, iy, N)] = val;
     }
     __syncthreads();
-    const cx<R>* res = fft_pingpong<R, true>(buf, scr, N, P, 1, P, g.rad, g.nrad, tw, 1);
+    const cx<R>* res;
+    if constexpr (NN > 0) res = fft_ct<R, true, P, NN>(buf, scr, tw, 1);
+    else res = fft_pingpong<R, true, P>(buf, scr, N, g.rad, g.nrad, tw, 1);
     cx<R>* dst = t2 + (size_t)blockIdx.y * t2_stride;
     float m = 0.f;
     for (int e = threadIdx.x; e < N * P; e += NTHR) {
         const int p = e % P, y = e / P, kz = kz0 + p;
         if (kz < g.nKz) {
-            const cx<R> v = res[y * P + p];
+            const cx<R> v = res[sidx<true, P>(p, y, N)];
             dst[((size_t)x * N + y) * g.nKz + kz] = v;
             m = fmaxf(m, (float)(fabs(v.re) + fabs(v.im)));
         }
@@ -280,7 +329,7 @@ __global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restri
 // complex DFT of length M = N/2:  Z_k = (H_k + conj H_{M-k})
 //   + i (H_k - conj H_{M-k}) e^{2 pi i k/N},  F[2m] = Re z_m, F[2m+1] = Im z_m,
 // with Im H_0 = Im H_M = 0 (the Hermitian part of the n_z = 0, N/2 planes).
-template <typename R, int P>
+template <typename R, int P, int NN>
 __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restrict__ t2,
                                                 size_t t2_stride, const cx<R>* __restrict__ twg,
                                                 const FieldDesc* __restrict__ fields, R* __restrict__ out,
@@ -289,10 +338,10 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
                                                 const unsigned* __restrict__ fmax2,
                                                 unsigned* __restrict__ f0max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = NN ? NN : g.n, M = N / 2;
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
-    cx<R>* buf = tw + g.n;
-    const int N = g.n, M = N / 2, ps = M + 1;
-    cx<R>* scr = buf + P * ps;
+    cx<R>* buf = tw + N;
+    cx<R>* scr = buf + smem_elems<false, P>(M);
     const int nyb = (N + P - 1) / P;
     const int x = blockIdx.x / nyb, y0 = (blockIdx.x % nyb) * P;
     const cx<R>* src = t2 + (size_t)blockIdx.y * t2_stride;
@@ -311,10 +360,12 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
             const cx<R> s = cadd(a, bc), d = csub(a, bc);
             z = cadd(s, cmuli(cmul(d, tw[k])));
         }
-        buf[p * ps + k] = z;
+        buf[sidx<false, P>(p, k, M)] = z;
     }
     __syncthreads();
-    const cx<R>* res = fft_pingpong<R, false>(buf, scr, M, P, ps, 1, g.rad_h, g.nrad_h, tw, 2);
+    const cx<R>* res;
+    if constexpr (NN > 0) res = fft_ct<R, false, P, NN / 2>(buf, scr, tw, 2);
+    else res = fft_pingpong<R, false, P>(buf, scr, M, g.rad_h, g.nrad_h, tw, 2);
     const FieldDesc fd = fields[blockIdx.y];
     R* dst = fd.out32 >= 0 ? out + (size_t)fd.out32 * out_stride : nullptr;
     const size_t plane = (size_t)N * N * M;   // 32-bit words (two 16-bit values) per field plane
@@ -328,7 +379,7 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
         const int m = e % M, p = e / M, y = y0 + p;
         if (y >= N) continue;
         const size_t pos = ((size_t)x * N + y) * M + m;
-        const cx<R> v = res[p * ps + m];
+        const cx<R> v = res[sidx<false, P>(p, m, M)];
         if (dst) {
             reinterpret_cast<cx<R>*>(dst)[pos] = v;
             mx = fmaxf(mx, fmaxf(fabsf((float)v.re), fabsf((float)v.im)));
@@ -369,34 +420,62 @@ struct FftCfg<double> {
     static constexpr int P = 4, P3 = 8;
 };
 
+template <typename R, int NN>
+cudaError_t launch_n(const FftGeom& g, const cx<float>* delta, const int16_t* shell_of, const float* radial,
+                     const FieldDesc* d_fields, int nfields, const cx<R>* tw, cx<R>* t1, cx<R>* t2, R* out,
+                     size_t out_stride, uint32_t* hi, uint32_t* lo, int f16, unsigned* fmax2, unsigned* f0max,
+                     cudaStream_t st) {
+    using C = FftCfg<R>;
+    const int N = g.n, M = N / 2;
+    const size_t t1_stride = (size_t)g.nK * N * g.nKz;
+    const size_t t2_stride = (size_t)N * N * g.nKz;
+    const size_t sm12 = sizeof(cx<R>) * ((size_t)N + 2 * (size_t)smem_elems<true, C::P>(N));
+    const size_t sm3 = sizeof(cx<R>) * ((size_t)N + 2 * (size_t)smem_elems<false, C::P3>(M));
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_pass1<R, C::P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm12)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_pass2<R, C::P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm12)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_pass3<R, C::P3, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)) !=
+        cudaSuccess)
+        return e;
+    const int nkzb = (g.nKz + C::P - 1) / C::P;
+    dim3 g1(g.nK * nkzb, nfields), g2(N * nkzb, nfields), g3(N * ((N + C::P3 - 1) / C::P3), nfields);
+    k_pass1<R, C::P, NN><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);
+    k_pass2<R, C::P, NN><<<g2, NTHR, sm12, st>>>(g, t1, t1_stride, tw, t2, t2_stride, d_fields, fmax2);
+    k_pass3<R, C::P3, NN><<<g3, NTHR, sm3, st>>>(g, t2, t2_stride, tw, d_fields, out, out_stride, hi, lo, f16,
+                                                 fmax2, f0max);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
+// Sizes of the workloads get kernels specialised at compile time; any other
+// supported size runs the same kernels with run-time radix lists.
 template <typename R>
 cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const int16_t* shell_of,
                               const float* radial, const FieldDesc* d_fields, int nfields,
                               const cx<R>* tw, cx<R>* t1, cx<R>* t2, R* out, size_t out_stride,
                               uint32_t* hi, uint32_t* lo, int f16, unsigned* fmax2, unsigned* f0max,
                               cudaStream_t st) {
-    using C = FftCfg<R>;
-    const int N = g.n, M = N / 2;
-    const size_t t1_stride = (size_t)g.nK * N * g.nKz;
-    const size_t t2_stride = (size_t)N * N * g.nKz;
-    const size_t sm12 = sizeof(cx<R>) * ((size_t)N + 2 * (size_t)N * C::P);
-    const size_t sm3 = sizeof(cx<R>) * ((size_t)N + 2 * (size_t)C::P3 * (M + 1));
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_pass1<R, C::P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm12)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_pass2<R, C::P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm12)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_pass3<R, C::P3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm3)) != cudaSuccess) return e;
-    const int nkzb = (g.nKz + C::P - 1) / C::P;
-    dim3 g1(g.nK * nkzb, nfields), g2(N * nkzb, nfields), g3(N * ((N + C::P3 - 1) / C::P3), nfields);
-    k_pass1<R, C::P><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);
-    k_pass2<R, C::P><<<g2, NTHR, sm12, st>>>(g, t1, t1_stride, tw, t2, t2_stride, d_fields, fmax2);
-    k_pass3<R, C::P3><<<g3, NTHR, sm3, st>>>(g, t2, t2_stride, tw, d_fields, out, out_stride, hi, lo, f16, fmax2,
-                                             f0max);
-    return cudaGetLastError();
+#define BSP_FFT_CASE(NV) \
+    case NV:             \
+        return launch_n<R, NV>(g, delta, shell_of, radial, d_fields, nfields, tw, t1, t2, out, out_stride, hi, lo, \
+                               f16, fmax2, f0max, st);
+    switch (g.n) {
+        BSP_FFT_CASE(64)
+        BSP_FFT_CASE(96)
+        BSP_FFT_CASE(128)
+        BSP_FFT_CASE(160)
+        BSP_FFT_CASE(256)
+        BSP_FFT_CASE(512)
+        default:
+            return launch_n<R, 0>(g, delta, shell_of, radial, d_fields, nfields, tw, t1, t2, out, out_stride, hi, lo,
+                                  f16, fmax2, f0max, st);
+    }
+#undef BSP_FFT_CASE
 }
 
 template cudaError_t launch_fft_fields<float>(const FftGeom&, const cx<float>*, const int16_t*, const float*,

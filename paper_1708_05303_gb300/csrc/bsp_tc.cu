@@ -19,8 +19,9 @@
 //   warps 12-15 drain the accumulator every `chunk` K-blocks (tcgen05.ld) and
 //               fold it into compensated FP32 (TwoSum hi + lo) running sums
 //               kept in tensor memory, written once to FP64 at the end.
-// Two smem stages and two accumulator buffers keep TMA, the CUDA-core
-// prologue, the MMAs and the epilogue overlapped.  Every mbarrier wait is
+// A three-stage TMA ring, two pair-product buffers and two accumulator
+// buffers keep TMA, the CUDA-core prologue, the MMAs and the epilogue
+// overlapped.  Every mbarrier wait is
 // bounded; on timeout the CTA records an error code, stops, waits (bounded)
 // for its own copies in flight and releases its tensor memory.
 #include <cuda.h>
@@ -34,7 +35,8 @@ namespace {
 constexpr int TC_M = 128;        // pairs per tile = MMA M
 constexpr int TC_NMAX = 128;     // field rows per tile = MMA N (max)
 constexpr int TC_KB = 64;        // x-points per K-block (128 bytes of 16-bit values)
-constexpr int TC_STAGES = 2;
+constexpr int NT = 3;            // TMA ring stages (F0 rows + field planes)
+constexpr int NA = 2;            // pair-product (A operand) buffers
 constexpr int TC_MAXSH = 64;     // F0 rows per tile
 constexpr int TC_THREADS = 512;  // 16 warps
 constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, N_PRO = 8, W_EPI0 = 12;
@@ -42,17 +44,18 @@ constexpr uint32_t TMEM_COLS = 512;   // acc0 [0,128) acc1 [128,256) hi [256,384
 constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
 
 struct TcSmem {
-    uint8_t a_hi[TC_STAGES][TC_M * 128];
-    uint8_t a_lo[TC_STAGES][TC_M * 128];
-    uint8_t b_hi[TC_STAGES][TC_NMAX * 128];
-    uint8_t b_lo[TC_STAGES][TC_NMAX * 128];
-    float f0[TC_STAGES][TC_MAXSH * TC_KB];
-    uint64_t full_tma[TC_STAGES], full_a[TC_STAGES], empty[TC_STAGES], acc_full[2], acc_empty[2];
+    uint8_t a_hi[NA][TC_M * 128];
+    uint8_t a_lo[NA][TC_M * 128];
+    uint8_t b_hi[NT][TC_NMAX * 128];
+    uint8_t b_lo[NT][TC_NMAX * 128];
+    float f0[NT][TC_MAXSH * TC_KB];
+    uint64_t tma_full[NT], tma_empty[NT], a_full[NA], a_empty[NA], acc_full[2], acc_empty[2];
     uint32_t tmem_base;
     volatile int abort;
     int2 pf[TC_M];
     float pscale[TC_M];
     float fscale[TC_NMAX];
+    TcWork w;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -196,17 +199,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const TcWork w = works[blockIdx.x];
+    if (tid < (int)(sizeof(TcWork) / sizeof(int)))
+        reinterpret_cast<int*>(&S.w)[tid] = reinterpret_cast<const int*>(works + blockIdx.x)[tid];
+    __syncthreads();
+    const TcWork& w = S.w;
     const int kb0 = blockIdx.y * kb_per_split;
     const int nkb = max(0, min(nkb_total, kb0 + kb_per_split) - kb0);
     const int nch = (nkb + CHUNK - 1) / CHUNK;
     const uint32_t N = (uint32_t)w.n;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(&S.full_tma[s], 1);
-            mbar_init(&S.full_a[s], N_PRO);
-            mbar_init(&S.empty[s], 1);
+        for (int s = 0; s < NT; ++s) {
+            mbar_init(&S.tma_full[s], 1);
+            mbar_init(&S.tma_empty[s], 1);
+        }
+        for (int s = 0; s < NA; ++s) {
+            mbar_init(&S.a_full[s], N_PRO);
+            mbar_init(&S.a_empty[s], 1);
         }
         for (int j = 0; j < 2; ++j) {
             mbar_init(&S.acc_full[j], 1);
@@ -251,34 +260,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int nfb = (w.nshell + 7) >> 3;
             const int nbb = (int)N >> 3;   // boxes including the padding box
             const uint32_t bytes = (uint32_t)nfb * 8 * TC_KB * 4 + (uint32_t)nbb * 1024 * 2;
-            int last_use[TC_STAGES] = {-1, -1};
+            int issued = 0;
             for (int k = 0; k < nkb && !S.abort; ++k) {
-                const int s = k & 1, use = k >> 1;
-                if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1)) {
+                const int s = k % NT, u = k / NT;
+                if (u > 0 && !mbar_wait(&S.tma_empty[s], (u - 1) & 1)) {
                     set_abort(S, err, 1);
                     break;
                 }
-                mbar_expect_tx(&S.full_tma[s], bytes);
+                mbar_expect_tx(&S.tma_full[s], bytes);
                 const int x0 = (kb0 + k) * TC_KB;
                 for (int j = 0; j < nfb; ++j)
-                    tma_load_2d(&S.f0[s][j * 8 * TC_KB], &tm_f0, x0, w.shell_lo + 8 * j, &S.full_tma[s]);
+                    tma_load_2d(&S.f0[s][j * 8 * TC_KB], &tm_f0, x0, w.shell_lo + 8 * j, &S.tma_full[s]);
                 for (int j = 0; j < nbb; ++j) {
                     const int f = w.box_field[j < w.nbox ? j : w.nbox - 1];
-                    tma_load_2d(&S.b_hi[s][j * 1024], &tm_hi, x0, f, &S.full_tma[s]);
-                    tma_load_2d(&S.b_lo[s][j * 1024], &tm_lo, x0, f, &S.full_tma[s]);
+                    tma_load_2d(&S.b_hi[s][j * 1024], &tm_hi, x0, f, &S.tma_full[s]);
+                    tma_load_2d(&S.b_lo[s][j * 1024], &tm_lo, x0, f, &S.tma_full[s]);
                 }
-                last_use[s] = use;
+                issued = k + 1;
             }
-            // copies in flight must land before the CTA can exit
-            for (int s = 0; s < TC_STAGES; ++s)
-                if (last_use[s] >= 0 && !mbar_wait(&S.full_tma[s], last_use[s] & 1)) atomicOr(err, 16);
+            // copies in flight must land before the CTA can exit: the last use of each stage
+            for (int k = max(0, issued - NT); k < issued; ++k)
+                if (!mbar_wait(&S.tma_full[k % NT], (k / NT) & 1)) atomicOr(err, 16);
         }
     } else if (warp == W_MMA) {
         if (lane == 0) {
             const uint32_t idesc = make_idesc(F16 ? 0u : 1u, N);
-            int last_s = -1, last_use = 0;
+            int done = 0;
             for (int k = 0; k < nkb && !S.abort; ++k) {
-                const int s = k & 1, use = k >> 1;
+                const int s = k % NT, u = k / NT, sa = k % NA, ua = k / NA;
                 const int c = k / CHUNK, j = c & 1;
                 const bool first = (k % CHUNK) == 0;
                 const bool last = (k % CHUNK) == CHUNK - 1 || k == nkb - 1;
@@ -286,13 +295,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     set_abort(S, err, 2);
                     break;
                 }
-                if (!mbar_wait(&S.full_tma[s], use & 1) || !mbar_wait(&S.full_a[s], use & 1)) {
+                if (!mbar_wait(&S.tma_full[s], u & 1) || !mbar_wait(&S.a_full[sa], ua & 1)) {
                     set_abort(S, err, 4);
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(j * 128);
-                const uint32_t ah = smem_u32(S.a_hi[s]), al = smem_u32(S.a_lo[s]);
+                const uint32_t ah = smem_u32(S.a_hi[sa]), al = smem_u32(S.a_lo[sa]);
                 const uint32_t bh = smem_u32(S.b_hi[s]), bl = smem_u32(S.b_lo[s]);
 #pragma unroll
                 for (int kk = 0; kk < TC_KB / 16; ++kk) {
@@ -303,25 +312,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         mma_16(d, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1u);
                     }
                 }
-                mma_commit(&S.empty[s]);
+                mma_commit(&S.tma_empty[s]);
+                mma_commit(&S.a_empty[sa]);
                 if (last) mma_commit(&S.acc_full[j]);
-                last_s = s;
-                last_use = use;
+                done = k + 1;
             }
             // the last MMAs must finish before tensor memory is released
-            if (last_s >= 0 && !mbar_wait(&S.empty[last_s], last_use & 1)) atomicOr(err, 32);
+            if (done > 0 && !mbar_wait(&S.a_empty[(done - 1) % NA], ((done - 1) / NA) & 1)) atomicOr(err, 32);
         }
     } else if (warp >= W_PRO0 && warp < W_PRO0 + N_PRO) {
         const int wr = warp - W_PRO0;
         for (int k = 0; k < nkb && !S.abort; ++k) {
-            const int s = k & 1, use = k >> 1;
-            if (!mbar_wait(&S.full_tma[s], use & 1)) {
+            const int s = k % NT, u = k / NT, sa = k % NA, ua = k / NA;
+            if (!mbar_wait(&S.tma_full[s], u & 1) || (ua > 0 && !mbar_wait(&S.a_empty[sa], (ua - 1) & 1))) {
                 set_abort(S, err, 8);
                 break;
             }
             const float* f0 = S.f0[s];
-            uint8_t* ah = S.a_hi[s];
-            uint8_t* al = S.a_lo[s];
+            uint8_t* ah = S.a_hi[sa];
+            uint8_t* al = S.a_lo[sa];
 #pragma unroll 4
             for (int r = 0; r < TC_M / N_PRO; ++r) {
                 const int i = wr * (TC_M / N_PRO) + r;
@@ -345,7 +354,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&S.full_a[s]);
+            if (lane == 0) mbar_arrive(&S.a_full[sa]);
         }
     } else if (warp >= W_EPI0) {
         const int q = warp & 3;

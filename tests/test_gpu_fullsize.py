@@ -1,0 +1,88 @@
+"""Parity at the full 512^3 / 64-shell workload, in the launch configuration
+bench.py times, on sampled bins the FP64 oracle can afford one by one.
+
+The oracle computes the raw sums T^l = sum_x F^l_a F_b F_c of the sampled
+bins with its own FFTs (its cost grows with the number of distinct fields, so
+the bins share shells).  The gate scale of each bin is max(|T|, rms), rms the
+root mean square over all bins of that multipole of B (taken from the FP32
+GPU result, which the small-grid tests tie to the oracle) converted to T.
+"""
+import numpy as np
+import pytest
+
+from paper_1708_05303_gb300.synth import FieldModel, linear_edges, make_field
+
+pytestmark = pytest.mark.gpu
+BOX = 1000.0
+N = 512
+SAMPLE = [(0, 0, 0), (20, 12, 10), (40, 21, 20), (63, 62, 61), (63, 40, 21), (40, 20, 20)]
+
+
+@pytest.fixture(scope="module")
+def results(ora):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_05303_gb300 import build
+
+    build.build()
+    from paper_1708_05303_gb300 import bsp
+
+    edges = linear_edges(64)
+    dk, _ = make_field(FieldModel(n=N, box=BOX, sigma_g=0.3), 1708 + 2)
+    d = torch.from_numpy(dk).cuda()
+    out = {}
+    base = bsp.Bispectrum(N, BOX, edges, (0, 2, 4), prec="fp32")
+    bins = [tuple(b) for b in base.bins]
+    counts = base.counts.copy()
+    out["fp32"] = (base.compute(d).cpu().numpy(), base.raw().cpu().numpy())
+    base.ws = None
+    torch.cuda.empty_cache()
+    for prec in ("split_f16", "split_bf16"):
+        est = bsp.Bispectrum(N, BOX, edges, (0, 2, 4), prec=prec, counts_from=base)
+        out[prec] = (est.compute(d).cpu().numpy(), est.raw().cpu().numpy())
+        assert bsp.bsp_device_status(est.plan) == 0
+        est.close()
+        del est
+        torch.cuda.empty_cache()
+    base.close()
+    idx = [bins.index(t) for t in SAMPLE]
+    r = ora.bispectrum(dk.astype(np.complex128), N, BOX, edges, (0, 2, 4), bins=SAMPLE)
+    return dict(bins=bins, counts=counts, idx=idx, gpu=out, ora=r)
+
+
+def gate_T(res, prec):
+    B32, _ = res["gpu"]["fp32"]
+    _, T = res["gpu"][prec]
+    r = res["ora"]
+    V, n3 = BOX ** 3, float(N) ** 3
+    rmsB = np.sqrt(np.mean(B32 ** 2, axis=1))
+    errs = []
+    for li in range(3):
+        for si, bi in enumerate(res["idx"]):
+            scale = max(abs(r["T"][li, si]), rmsB[li] * V * n3 * res["counts"][bi])
+            errs.append(abs(T[li, bi] - r["T"][li, si]) / scale)
+    return max(errs)
+
+
+def test_counts_of_sampled_bins_match_oracle(results):
+    r = results["ora"]
+    assert np.array_equal(np.asarray(results["counts"])[results["idx"]], r["counts"])
+
+
+def test_fp32_fullsize(results):
+    e = gate_T(results, "fp32")
+    print("fp32 512^3 sampled gate error %.3g" % e)
+    assert e <= 1e-5
+
+
+def test_split_f16_fullsize(results):
+    e = gate_T(results, "split_f16")
+    print("split_f16 512^3 sampled gate error %.3g" % e)
+    assert e <= 1e-5
+
+
+def test_split_bf16_fullsize_reported(results):
+    e = gate_T(results, "split_bf16")
+    print("split_bf16 512^3 sampled gate error %.3g" % e)
+    assert e <= 2e-4
