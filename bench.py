@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--shells", type=int, default=64)
+    ap.add_argument("--width", type=float, default=2.0, help="shell width in k_f")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "split_bf16", "split_f16", "bf16"])
     ap.add_argument("--chunk", type=int, default=0, help="tensor-core FP32 accumulation chunk (points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -53,12 +54,12 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n, shells):
+def workload(n, shells, width=2.0):
     from paper_1708_05303_gb300.synth import linear_edges
 
-    edges = linear_edges(shells)
-    desc = ("%d^3 grid, L=%g Mpc/h, sigma_g=0.3 quadratic+Kaiser field, %d shells of width 2 k_f from k_f, "
-            "l=0,2,4" % (n, BOX, shells))
+    edges = linear_edges(shells, width)
+    desc = ("%d^3 grid, L=%g Mpc/h, sigma_g=0.3 quadratic+Kaiser field, %d shells of width %g k_f from k_f, "
+            "l=0,2,4" % (n, BOX, shells, width))
     return edges, desc
 
 
@@ -154,7 +155,7 @@ def run_reference(args):
         return 0
     import numpy as np
 
-    edges, desc = workload(args.n, args.shells)
+    edges, desc = workload(args.n, args.shells, args.width)
     import oracle
 
     dk = make_input(args.n)
@@ -202,7 +203,7 @@ def main():
     B.build()
     from paper_1708_05303_gb300 import bsp
 
-    edges, desc = workload(args.n, args.shells)
+    edges, desc = workload(args.n, args.shells, args.width)
     dk = make_input(args.n)
     t0 = time.perf_counter()
     est = bsp.Bispectrum(args.n, BOX, edges, (0, 2, 4), prec=args.prec, host_staging=not args.no_e2e)

@@ -75,6 +75,11 @@ typedef enum {
                             operands (22 significant bits), FP32 accumulate */
 } bsp_precision;
 
+/* Plan flags. */
+enum {
+    BSP_SHOT_NOISE = 1u   /* reserve workspace for Poisson shot-noise subtraction (BSP_FP32 only) */
+};
+
 typedef struct bsp_plan bsp_plan;
 
 /*
@@ -86,12 +91,102 @@ typedef struct bsp_plan bsp_plan;
  *   n_ell    1..3 entries of ells, each in {0, 2, 4}, strictly ascending
  *            (odd l vanish by parity, Sec. 3.5).
  *   prec     a bsp_precision.
- *   flags    0 (reserved).
+ *   flags    0 or BSP_SHOT_NOISE (triples the field workspace; BSP_FP32 only).
  * Host-only: allocates the plan's small device tables on the current device.
  */
 bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells,
                            const double* edges_kf, int n_ell, const int* ells,
                            int prec, unsigned flags);
+
+/*
+ * Create a plan for the modal estimator (Sec. 3.5, Eq. betaEst and its RSD
+ * form): fields M^l_p(x) = sum_n e^{ik.x} w_l(mu) R_p[|n|^2] delta(n), one
+ * per 1-D mode p and multipole, and the raw projections
+ *   <<B_l | Q_pqr>> = (1/(n^3 V^3)) sum_x sum_{l1+l2+l3=l} {M^(l1) M^(l2) M^(l3)}_pqr
+ * for every p <= q <= r (the {} average over the 6 orderings of (p, q, r);
+ * l = 2 needs 3 terms, l = 4 six, l = 0 one -- Eq. Bisp_ell and its footnote).
+ *   n_funcs  1-D modes (1..64).
+ *   radial   HOST FP64 [n_funcs][3 (n/2)^2 + 1]: R_p indexed by the integer
+ *            |n|^2, e.g. q_p(k)/sqrt(k P(k)) from bsp_modal_radial_powerlaw.
+ *            Copied (as FP32) into the plan.
+ *   ells, prec as for bsp_plan_create; flags 0.
+ * No counts are needed; bsp_counts and bsp_compute reject modal plans.
+ */
+bsp_status bsp_plan_create_modal(bsp_plan** out, int n, double box, int n_funcs, const double* radial,
+                                 int n_ell, const int* ells, int prec, unsigned flags);
+
+/* n_funcs and the number of triplets p <= q <= r, n_funcs (n_funcs+1)(n_funcs+2)/6. */
+bsp_status bsp_modal_size(const bsp_plan* plan, int* n_funcs, int* n_trip);
+
+/*
+ * Raw modal projections <<B_l | Q_pqr>> (see bsp_plan_create_modal) into
+ * S, device FP64 [n_ell][n_trip], triplets (p <= q <= r) in lexicographic
+ * order.  delta_k and ws as for bsp_compute.  Asynchronous on `stream`.
+ */
+bsp_status bsp_modal_compute(bsp_plan* plan, const void* delta_k, void* ws, void* stream, double* S);
+
+/*
+ * Host helpers of the modal estimator (FP64, no GPU).
+ * bsp_modal_radial_powerlaw: table [n_modes][3 (n/2)^2 + 1] of
+ *   q_p(k) / sqrt(k P(k)) (sqrt_k != 0, Sec. 3.5) or q_p(k) / sqrt(P(k)),
+ *   k = k_f |n|, P(k) = amp k^n_s, q_p the shifted Legendre polynomial P_p on
+ *   [kmin, kmax] (zero outside); 0 at n = 0.
+ * bsp_modal_modes: the first n_keep 3-D modes (p <= q <= r), ordered by
+ *   (p+q+r, p, q, r), as int32 [n_keep][3].
+ * bsp_modal_gamma: gamma_nm = <<Q_n | Q_m>> = (1/8 pi^4) int_V dk1 dk2 dk3
+ *   Q_n Q_m over the tetrapyd V = {k_i in [kmin, kmax], 2 max k_i <= sum k_i}
+ *   (Sec. 3.5), Q_n the symmetrised product of Eq. Qn; piecewise
+ *   Gauss-Legendre with npts nodes per piece (exact for polynomial degree
+ *   < 2 npts per variable).  gamma is FP64 [n_keep][n_keep].
+ * bsp_modal_project: beta = gamma^-1 S for n_rhs right-hand sides
+ *   (S, beta: [n_rhs][n_keep]) by Cholesky (Eq. betaCalc); BSP_EINVAL if
+ *   gamma is not positive definite.
+ */
+bsp_status bsp_modal_radial_powerlaw(int n, double box, int n_modes, double kmin, double kmax, double amp,
+                                     double n_s, int sqrt_k, double* table);
+bsp_status bsp_modal_modes(int n_modes_1d, int n_keep, int32_t* modes);
+bsp_status bsp_modal_gamma(int n_keep, const int32_t* modes, double kmin, double kmax, int npts,
+                           double* gamma);
+bsp_status bsp_modal_project(int n_keep, const double* gamma, int n_rhs, const double* S, double* beta);
+
+/*
+ * Batches of mock realisations on uneven grids, and their covariance (the
+ * covariance from mock catalogues of Sec. 1 and Sec. 3.1).
+ *
+ * bsp_batch_create: one plan per grid size (sizes[0..n_sizes), <= 8), same
+ *   shells, multipoles and precision (flags 0).
+ * bsp_batch_workspace_size: device workspace for prepare and run (one plan
+ *   workspace shared by all sizes, two input buffers, a B staging area).
+ * bsp_batch_prepare: counts for every size (BSP_EINVAL if the sizes disagree
+ *   on the valid bins: rows would not line up); with autotune != 0 times
+ *   the contraction grid {1024, 2048, 4096} x FFT batch {4, 16, 64} per
+ *   size and keeps the fastest; then captures bsp_compute into one CUDA
+ *   graph per (size, input buffer).  Synchronises `stream`.
+ * bsp_batch_info / bsp_batch_bins: n_bins, the autotuner's choices and times
+ *   (arrays of n_sizes), and the common bins / counts.
+ * bsp_batch_run: for m < n_mocks, copies the complex64 half spectrum at host
+ *   pointer delta_host[m] (pinned memory for overlap) of grid
+ *   sizes[size_index[m]] into an input buffer on an internal copy stream while
+ *   the previous mock's graph runs, replays that size's graph on `stream`,
+ *   and stores B into rows (device FP64 [n_mocks][n_ell * n_bins]).
+ *   Asynchronous on `stream`; the host arrays must stay valid until it
+ *   completes.
+ * bsp_covariance: mean (device FP64 [d]) and unbiased covariance (device
+ *   FP64 [d][d]) of the m >= 2 rows of a device FP64 [m][d] matrix, two
+ *   passes (mean, then centred products) in a fixed order.
+ */
+typedef struct bsp_batch bsp_batch;
+bsp_status bsp_batch_create(bsp_batch** out, int n_sizes, const int* sizes, double box, int n_shells,
+                            const double* edges_kf, int n_ell, const int* ells, int prec, unsigned flags);
+void bsp_batch_destroy(bsp_batch* batch);
+bsp_status bsp_batch_workspace_size(const bsp_batch* batch, size_t* bytes);
+bsp_status bsp_batch_prepare(bsp_batch* batch, void* ws, void* stream, int autotune);
+bsp_status bsp_batch_info(const bsp_batch* batch, int* n_bins, int* tuned_ctas, int* tuned_fb,
+                          double* tuned_ms);
+bsp_status bsp_batch_bins(const bsp_batch* batch, int32_t* abc, double* counts);
+bsp_status bsp_batch_run(bsp_batch* batch, int n_mocks, const int* size_index, const void* const* delta_host,
+                         void* ws, void* stream, double* rows);
+bsp_status bsp_covariance(int m, int d, const double* rows, double* mean, double* cov, void* stream);
 
 /* Release the plan and its device tables (NULL is ignored). */
 void bsp_plan_destroy(bsp_plan* plan);
@@ -130,8 +225,14 @@ bsp_status bsp_plan_bins(const bsp_plan* plan, int* n_bins, int32_t* abc, double
  * B^l for every valid bin (Eq. Standard_ell_Estim): enqueue filter ->
  * inverse FFTs -> contraction -> FP64 reduction and normalisation.
  *   delta_k  device, complex64 [n][n][n/2+1] (read only).
- *   nbar     mean number density for Poisson shot-noise subtraction, or
- *            0 for none (BSP_EUNSUPPORTED if > 0 in this build).
+ *   nbar     mean number density n_p / V of the particles behind delta for
+ *            Poisson shot-noise subtraction, or 0 for none.  The term
+ *            subtracted per triangle is (the paper is silent; this is the
+ *            Poisson expectation with P_tot = |delta|^2 / V)
+ *              w_l(mu_1) [(|d1|^2 + |d2|^2 + |d3|^2)/(V nbar) - 2/nbar^2],
+ *            evaluated as three more contractions of the same shape.
+ *            Needs a plan created with BSP_SHOT_NOISE (else BSP_EINVAL;
+ *            BSP_EUNSUPPORTED on tensor-core plans).
  *   ws       device workspace of bsp_workspace_size bytes.
  *   B        device FP64 [n_ell][n_bins], written.
  * Asynchronous on `stream`; BSP_ESTATE before bsp_counts.
@@ -162,8 +263,15 @@ bsp_status bsp_last_raw(const bsp_plan* plan, void* ws, void* stream, double* T)
 bsp_status bsp_plan_stats(const bsp_plan* plan, double* st);
 
 /*
+ * Schedule knobs (the batch runner's autotuner sets them): the number of
+ * CTAs the CUDA-core contraction aims at (0 = keep; <= 4096) and the number
+ * of fields transformed per FFT launch (0 = keep; capped by the workspace).
+ */
+bsp_status bsp_plan_tune(bsp_plan* plan, int target_ctas, int fft_batch);
+
+/*
  * Tensor-core paths only: the number of x-points (a multiple of 64, 64 ..
- * 2^20; default 1024) summed in an FP32 tensor-memory accumulator before it
+ * 2^20; default 256) summed in an FP32 tensor-memory accumulator before it
  * is folded into the compensated running sums.  Shorter chunks are more
  * accurate and cost more epilogue work.
  */
@@ -188,6 +296,7 @@ bsp_status bsp_device_status(bsp_plan* plan, int* code);
  */
 bsp_status bsp_set_profiling(bsp_plan* plan, int on);
 bsp_status bsp_phase_times(bsp_plan* plan, double* ms, int* ncalls, int* launches);
+
 
 
 /* Human-readable text for a status, and the last CUDA error text seen by

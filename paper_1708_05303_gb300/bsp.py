@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbsp.so")
 
 BSP_OK, BSP_EINVAL, BSP_ENOMEM, BSP_ECUDA, BSP_EUNSUPPORTED, BSP_ETIMEOUT, BSP_ESTATE = 0, -1, -2, -3, -4, -5, -6
 BSP_FP32, BSP_SPLIT_BF16, BSP_BF16, BSP_SPLIT_F16 = 0, 1, 2, 3
+BSP_SHOT_NOISE = 1
 PRECISIONS = {"fp32": BSP_FP32, "split_bf16": BSP_SPLIT_BF16, "bf16": BSP_BF16, "split_f16": BSP_SPLIT_F16}
 
 # (name, restype, argtypes) of every exported entry point declared in include/bsp.h
@@ -28,6 +29,17 @@ _SIGS = [
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_uint]),
     ("bsp_plan_destroy", None, [_P]),
+    ("bsp_plan_create_modal", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_double, ctypes.c_int, _P,
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                             ctypes.c_uint]),
+    ("bsp_modal_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("bsp_modal_compute", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("bsp_modal_radial_powerlaw", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                 _P]),
+    ("bsp_modal_modes", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P]),
+    ("bsp_modal_gamma", ctypes.c_int, [ctypes.c_int, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P]),
+    ("bsp_modal_project", ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     ("bsp_workspace_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("bsp_host_staging_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("bsp_counts", ctypes.c_int, [_P, _P, _P]),
@@ -38,6 +50,16 @@ _SIGS = [
     ("bsp_last_raw", ctypes.c_int, [_P, _P, _P, _P]),
     ("bsp_device_status", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("bsp_set_accumulation_chunk", ctypes.c_int, [_P, ctypes.c_int]),
+    ("bsp_plan_tune", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    ("bsp_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_double, ctypes.c_int, _P,
+                                        ctypes.c_int, _P, ctypes.c_int, ctypes.c_uint]),
+    ("bsp_batch_destroy", None, [_P]),
+    ("bsp_batch_workspace_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    ("bsp_batch_prepare", ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    ("bsp_batch_info", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P, _P, _P]),
+    ("bsp_batch_bins", ctypes.c_int, [_P, _P, _P]),
+    ("bsp_batch_run", ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    ("bsp_covariance", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     ("bsp_plan_stats", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("bsp_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
     ("bsp_phase_times", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
@@ -107,6 +129,62 @@ def bsp_plan_create(n: int, box: float, edges, ells=(0, 2, 4), prec: int = BSP_F
                              l_.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(prec), int(flags))
     _check(st, "bsp_plan_create")
     return h.value
+
+
+def bsp_plan_create_modal(n: int, box: float, radial: np.ndarray, ells=(0, 2, 4), prec: int = BSP_FP32,
+                          flags: int = 0) -> int:
+    lib = load()
+    tab = np.ascontiguousarray(radial, dtype=np.float64)
+    l_ = np.ascontiguousarray(ells, dtype=np.int32)
+    h = _P()
+    st = lib.bsp_plan_create_modal(ctypes.byref(h), int(n), float(box), int(tab.shape[0]), tab.ctypes.data,
+                                   int(l_.size), l_.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(prec),
+                                   int(flags))
+    _check(st, "bsp_plan_create_modal")
+    return h.value
+
+
+def bsp_modal_size(plan: int):
+    nf, nt = ctypes.c_int(), ctypes.c_int()
+    _check(load().bsp_modal_size(plan, ctypes.byref(nf), ctypes.byref(nt)), "bsp_modal_size")
+    return nf.value, nt.value
+
+
+def bsp_modal_compute(plan: int, delta_k, ws, S, stream=None):
+    _check(load().bsp_modal_compute(plan, _dptr(delta_k), _dptr(ws), _stream_handle(stream), _dptr(S)),
+           "bsp_modal_compute")
+
+
+def bsp_modal_radial_powerlaw(n: int, box: float, n_modes: int, kmin: float, kmax: float, amp: float, n_s: float,
+                              sqrt_k: bool = True) -> np.ndarray:
+    tab = np.zeros((n_modes, 3 * (n // 2) ** 2 + 1))
+    _check(load().bsp_modal_radial_powerlaw(int(n), float(box), int(n_modes), float(kmin), float(kmax), float(amp),
+                                            float(n_s), int(bool(sqrt_k)), tab.ctypes.data),
+           "bsp_modal_radial_powerlaw")
+    return tab
+
+
+def bsp_modal_modes(n_modes_1d: int, n_keep: int) -> np.ndarray:
+    m = np.zeros((n_keep, 3), dtype=np.int32)
+    _check(load().bsp_modal_modes(int(n_modes_1d), int(n_keep), m.ctypes.data), "bsp_modal_modes")
+    return m
+
+
+def bsp_modal_gamma(modes: np.ndarray, kmin: float, kmax: float, npts: int = 24) -> np.ndarray:
+    m = np.ascontiguousarray(modes, dtype=np.int32).reshape(-1, 3)
+    g = np.zeros((m.shape[0], m.shape[0]))
+    _check(load().bsp_modal_gamma(int(m.shape[0]), m.ctypes.data, float(kmin), float(kmax), int(npts),
+                                  g.ctypes.data), "bsp_modal_gamma")
+    return g
+
+
+def bsp_modal_project(gamma: np.ndarray, S: np.ndarray) -> np.ndarray:
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    s = np.ascontiguousarray(np.atleast_2d(S), dtype=np.float64)
+    beta = np.zeros_like(s)
+    _check(load().bsp_modal_project(int(g.shape[0]), g.ctypes.data, int(s.shape[0]), s.ctypes.data,
+                                    beta.ctypes.data), "bsp_modal_project")
+    return beta
 
 
 def bsp_plan_destroy(plan: int):
@@ -197,17 +275,120 @@ def bsp_version() -> int:
     return int(load().bsp_version())
 
 
+class Batch:
+    """Mock ensemble on uneven grids through bsp_batch_*: ``run(deltas,
+    size_index)`` returns the device FP64 rows [n_mocks][n_ell*n_bins];
+    ``covariance(rows)`` returns (mean, cov) on the device."""
+
+    def __init__(self, sizes, box, edges, ells=(0, 2, 4), prec="fp32", autotune=True, stream=None):
+        import torch
+
+        lib = load()
+        self.sizes = [int(v) for v in sizes]
+        self.ells = tuple(ells)
+        sz = np.ascontiguousarray(self.sizes, dtype=np.int32)
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        l_ = np.ascontiguousarray(ells, dtype=np.int32)
+        h = _P()
+        _check(lib.bsp_batch_create(ctypes.byref(h), len(self.sizes), sz.ctypes.data, float(box), int(e.size - 1),
+                                    e.ctypes.data, int(l_.size), l_.ctypes.data, PRECISIONS.get(prec, prec), 0),
+               "bsp_batch_create")
+        self.h = h.value
+        n = ctypes.c_size_t()
+        _check(lib.bsp_batch_workspace_size(self.h, ctypes.byref(n)), "bsp_batch_workspace_size")
+        self.ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device="cuda")
+        _check(lib.bsp_batch_prepare(self.h, _dptr(self.ws), _stream_handle(stream), int(bool(autotune))),
+               "bsp_batch_prepare")
+        nb = ctypes.c_int()
+        ctas = np.zeros(len(self.sizes), dtype=np.int32)
+        fb = np.zeros(len(self.sizes), dtype=np.int32)
+        ms = np.zeros(len(self.sizes))
+        _check(lib.bsp_batch_info(self.h, ctypes.byref(nb), ctas.ctypes.data, fb.ctypes.data, ms.ctypes.data),
+               "bsp_batch_info")
+        self.nbins = nb.value
+        self.tuning = {"target_ctas": ctas.tolist(), "fft_batch": fb.tolist(), "ms": ms.tolist()}
+        self.bins = np.zeros((self.nbins, 3), dtype=np.int32)
+        self.counts = np.zeros(self.nbins)
+        _check(lib.bsp_batch_bins(self.h, self.bins.ctypes.data, self.counts.ctypes.data), "bsp_batch_bins")
+
+    def run(self, deltas, size_index, rows=None, stream=None):
+        """deltas: host complex64 arrays (pinned torch tensors or numpy)."""
+        import torch
+
+        m = len(deltas)
+        d = len(self.ells) * self.nbins
+        if rows is None:
+            rows = torch.empty((m, d), dtype=torch.float64, device="cuda")
+        ptrs = (ctypes.c_void_p * m)(*[(x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data) for x in deltas])
+        si = np.ascontiguousarray(size_index, dtype=np.int32)
+        _check(load().bsp_batch_run(self.h, m, si.ctypes.data, ptrs, _dptr(self.ws), _stream_handle(stream),
+                                    _dptr(rows)), "bsp_batch_run")
+        return rows
+
+    @staticmethod
+    def covariance(rows, stream=None):
+        import torch
+
+        m, d = rows.shape
+        mean = torch.empty(d, dtype=torch.float64, device="cuda")
+        cov = torch.empty((d, d), dtype=torch.float64, device="cuda")
+        _check(load().bsp_covariance(int(m), int(d), _dptr(rows), _dptr(mean), _dptr(cov), _stream_handle(stream)),
+               "bsp_covariance")
+        return mean, cov
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bsp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Modal:
+    """A modal plan plus its workspace: ``compute(delta_k)`` returns the raw
+    projections <<B_l|Q_pqr>> [n_ell][n_trip] (FP64, device)."""
+
+    def __init__(self, n, box, radial, ells=(0, 2, 4), prec="fp32"):
+        import torch
+
+        self.n, self.box, self.ells = int(n), float(box), tuple(ells)
+        self.plan = bsp_plan_create_modal(n, box, radial, ells, PRECISIONS.get(prec, prec))
+        self.nf, self.ntrip = bsp_modal_size(self.plan)
+        self.ws = torch.empty(max(bsp_workspace_size(self.plan), 256), dtype=torch.uint8, device="cuda")
+        self.S = torch.empty((len(self.ells), self.ntrip), dtype=torch.float64, device="cuda")
+
+    def compute(self, delta_k, stream=None):
+        bsp_modal_compute(self.plan, delta_k, self.ws, self.S, stream)
+        return self.S
+
+    def close(self):
+        if getattr(self, "plan", None):
+            bsp_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Bispectrum:
     """A plan plus its device workspace (PyTorch-allocated), counts done on
     construction.  ``compute(delta_k)`` returns B [n_ell][n_bins] (FP64,
     device) for a complex64 [n][n][n/2+1] CUDA tensor."""
 
     def __init__(self, n, box, edges, ells=(0, 2, 4), prec="fp32", host_staging=False, stream=None,
-                 counts_from=None, ws=None):
+                 counts_from=None, ws=None, shot_noise=False):
         import torch
 
         self.n, self.box, self.ells = int(n), float(box), tuple(ells)
-        self.plan = bsp_plan_create(n, box, edges, ells, PRECISIONS.get(prec, prec))
+        self.plan = bsp_plan_create(n, box, edges, ells, PRECISIONS.get(prec, prec),
+                                    BSP_SHOT_NOISE if shot_noise else 0)
         nbytes = bsp_workspace_size(self.plan)
         if host_staging:
             nbytes += bsp_host_staging_size(self.plan)

@@ -183,10 +183,57 @@ struct TcSched {
     std::vector<TcWork> works;
     std::vector<int2> pairs;
     std::vector<BinLoc> loc;
-    int nsplit = 1;
+    std::vector<TcUnit> units;
+    int lsup = 1, nsup = 1;
 };
 
-TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, int nsh, size_t npts) {
+// Persistent units: each work gets CTAs in proportion to its cost (its MMA N
+// plus a constant for the pair-product prologue), all CTAs together about
+// one per SM; every super-segment of lsup K-blocks is split among the work's
+// CTAs, so all works sweep x at the same pace and share the fields in L2.
+void assign_units(TcSched& h, size_t npts, int nsm) {
+    const int nw = (int)h.works.size();
+    const long long nkb = (long long)((npts + 63) / 64);
+    const int maxc = (int)std::max<long long>(1, nkb / 16);
+    std::vector<int> c(nw, 1);
+    if (nw < nsm) {
+        double wsum = 0;
+        for (auto& w : h.works) wsum += w.n + 48.0;
+        int used = 0;
+        std::vector<std::pair<double, int>> frac;
+        for (int i = 0; i < nw; ++i) {
+            const double want = nsm * (h.works[i].n + 48.0) / wsum;
+            c[i] = std::max(1, (int)want);
+            used += c[i];
+            frac.push_back({want - (int)want, i});
+        }
+        std::sort(frac.begin(), frac.end(), [](auto& a, auto& b) { return a.first > b.first; });
+        for (size_t k = 0; used < nsm && k < frac.size(); ++k, ++used) ++c[frac[k].second];
+    }
+    int cmax = 1;
+    for (int i = 0; i < nw; ++i) {
+        c[i] = std::min(c[i], maxc);
+        cmax = std::max(cmax, c[i]);
+    }
+    h.lsup = (int)std::min<long long>(nkb, std::max(16 * cmax, 64));
+    h.nsup = (int)((nkb + h.lsup - 1) / h.lsup);
+    std::vector<int> first(nw);
+    h.units.clear();
+    for (int i = 0; i < nw; ++i) {
+        first[i] = (int)h.units.size();
+        for (int j = 0; j < c[i]; ++j) {
+            const int a = (int)((long long)j * h.lsup / c[i]), b = (int)((long long)(j + 1) * h.lsup / c[i]);
+            h.units.push_back(TcUnit{i, a, b - a, 0});
+        }
+    }
+    for (BinLoc& L : h.loc) {
+        const int w = L.work;
+        L.work = first[w];
+        L.pad = c[w];
+    }
+}
+
+TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, int nsh, size_t npts, int nsm) {
     TcSched h;
     std::map<std::pair<int, int>, int> pidx;
     for (auto& t : bins) pidx[{t[1], t[2]}] = 0;
@@ -241,9 +288,7 @@ TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, i
             const int box = (int)si * t.nbs + (bins[b][0] - t.alo) / 8;
             h.loc[si * bins.size() + b] = BinLoc{t.work0 + box / 16, p - t.p0, 8 * (box % 16) + (bins[b][0] - t.alo) % 8, 0};
         }
-    const int nw = std::max<int>(1, (int)h.works.size());
-    const long long nkb = (long long)((npts + 63) / 64);
-    h.nsplit = (int)std::max<long long>(1, std::min<long long>((1216 + nw - 1) / nw, std::max<long long>(1, nkb / 16)));
+    assign_units(h, npts, nsm);
     return h;
 }
 
@@ -303,10 +348,25 @@ struct bsp_plan {
     int prec = 0;
     FftGeom geom{};
     int target_ctas = 2048;
+    int fb_cap = 1;                   // FFT batch width the workspace was sized for
     int16_t* d_shell_of = nullptr;
     cx<float>* d_tw32 = nullptr;
     cx<double>* d_tw64 = nullptr;
-    FieldDesc* d_fd_delta = nullptr;  // [nslot*nsh]
+    FieldDesc* d_fd_delta = nullptr;  // [nslot*nsh], or [3][nslot*nsh] with shot noise
+    bool shot = false;                // BSP_SHOT_NOISE: workspace for the shot-noise fields
+    // modal plans (Sec. 3.5): fields M^l_p from radial tables, all (a; b >= c) sums
+    bool modal = false;
+    int slot2 = -1;                   // slot of l = 2 (the U term of l = 4), or -1
+    bool need_u = false;
+    float* d_radial = nullptr;        // [n_funcs][n2max + 1]
+    int* d_ells = nullptr;
+    HostSched u_sched;                // rows M0_a, pairs M2_b M2_c
+    DevSched u_dev;
+    TcSched tc_u_sched;
+    TcWork* d_tcu_works = nullptr;
+    int2* d_tcu_pairs = nullptr;
+    BinLoc* d_tcu_loc = nullptr;
+    size_t upart_bytes = 0, tcu_part_bytes = 0, tfull_bytes = 0, ufull_bytes = 0;
     FieldDesc* d_fd_unit = nullptr;   // [nsh]
     // candidate bins (superset of the valid ones) and their counting schedule
     BinList cand;
@@ -324,12 +384,15 @@ struct bsp_plan {
     int nprod = 3;
     FieldDesc* d_fd_tc = nullptr;     // [nslot*nsh]
     TcSched tc_sched;
+    int nsm = 148;
+    TcUnit* d_tc_units = nullptr;
+    TcUnit* d_tcu_units = nullptr;
     TcWork* d_tc_works = nullptr;
     int2* d_tc_pairs = nullptr;
     BinLoc* d_tc_loc = nullptr;
     int* d_err = nullptr;
     unsigned* d_fmax = nullptr;   // per-field magnitude bounds for the 16-bit scaling
-    int chunk_kb = 16;            // K-blocks (64 points each) per FP32 tensor-memory accumulation
+    int chunk_kb = 4;             // K-blocks (64 points each) per FP32 tensor-memory accumulation
     size_t f0_bytes = 0, plane_bytes = 0, tc_part_bytes = 0;
     // workspace layout
     size_t fld32_bytes = 0, fld64_bytes = 0, t12_bytes32 = 0, t12_bytes64 = 0;
@@ -348,6 +411,9 @@ struct bsp_plan {
         cudaFree(d_fd_delta); cudaFree(d_fd_unit); cudaFree(d_counts);
         cudaFree(d_fd_tc); cudaFree(d_tc_works); cudaFree(d_tc_pairs); cudaFree(d_tc_loc); cudaFree(d_err);
         cudaFree(d_fmax);
+        cudaFree(d_tc_units); cudaFree(d_tcu_units);
+        cudaFree(d_radial); cudaFree(d_ells); cudaFree(d_tcu_works); cudaFree(d_tcu_pairs); cudaFree(d_tcu_loc);
+        u_dev.release();
         cand_dev.release(); comp_dev.release();
     }
     size_t npts() const { return (size_t)n * n * n; }
@@ -373,12 +439,21 @@ Layout layout_compute(const bsp_plan* p) {
     t12_sizes(p->geom, sizeof(float), &t1, &t2);
     L.fields = 0;
     if (p->tc) {
-        // F0 (FP32, nsh fields) | hi planes | lo planes (16-bit, nslot*nsh fields each)
+        // F0 (FP32 pair factors) | hi planes | lo planes (16-bit, nslot*nsh fields each)
         L.t1 = L.fields + p->f0_bytes + 2 * p->plane_bytes;
         L.t2 = L.t1 + t1 * p->fb32;
         L.partial = L.t2 + t2 * p->fb32;
-        L.tout = L.partial + p->tc_part_bytes;
-        L.cnt = L.tout + p->tout_bytes;
+        L.tout = L.partial + p->tc_part_bytes + p->tcu_part_bytes;
+        L.cnt = L.tout + p->tout_bytes + p->tfull_bytes + p->ufull_bytes;
+        L.end = L.cnt;
+        return L;
+    }
+    if (p->modal) {
+        L.t1 = L.fields + p->fld32_bytes;
+        L.t2 = L.t1 + t1 * p->fb32;
+        L.partial = L.t2 + t2 * p->fb32;
+        L.tout = L.partial + p->part_bytes + p->upart_bytes;
+        L.cnt = L.tout + p->tfull_bytes + p->ufull_bytes;
         L.end = L.cnt;
         return L;
     }
@@ -439,7 +514,7 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     if (!out) return BSP_EINVAL;
     *out = nullptr;
     if (!good_size(n) || !(box > 0) || !std::isfinite(box) || n_shells < 1 || n_shells > 64 || !edges_kf ||
-        n_ell < 1 || n_ell > 3 || !ells || flags != 0)
+        n_ell < 1 || n_ell > 3 || !ells || (flags & ~(unsigned)BSP_SHOT_NOISE))
         return BSP_EINVAL;
     for (int i = 0; i <= n_shells; ++i)
         if (!(edges_kf[i] > 0) || !std::isfinite(edges_kf[i]) || (i && !(edges_kf[i] > edges_kf[i - 1])))
@@ -451,6 +526,7 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     }
     if (prec != BSP_FP32 && prec != BSP_SPLIT_BF16 && prec != BSP_BF16 && prec != BSP_SPLIT_F16)
         return BSP_EUNSUPPORTED;
+    if ((flags & BSP_SHOT_NOISE) && prec != BSP_FP32) return BSP_EUNSUPPORTED;
 
     bsp_plan* p = new (std::nothrow) bsp_plan();
     if (!p) return BSP_ENOMEM;
@@ -460,6 +536,13 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     p->edges.assign(edges_kf, edges_kf + n_shells + 1);
     p->ells.assign(ells, ells + n_ell);
     p->prec = prec;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            p->nsm = sms;
+    }
+    p->shot = (flags & BSP_SHOT_NOISE) != 0;
     p->tc = prec != BSP_FP32;
     p->nprod = prec == BSP_BF16 ? 1 : 3;
     p->slot_ell.push_back(0);
@@ -508,6 +591,15 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
             fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, f, -1, {0, 0, 0}});
             fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, s == 0 ? a : -1, f, {0, 0, 0}});
         }
+    if (p->shot) {
+        // S^l_a = w_l |delta|^2 on a, then W^l_a = w_l on a (W^0 = the unit fields I)
+        const int nfs = p->nslot() * n_shells;
+        for (int kind = 0; kind < 2; ++kind)
+            for (int s = 0; s < p->nslot(); ++s)
+                for (int a = 0; a < n_shells; ++a)
+                    fdd.push_back(FieldDesc{a, p->slot_ell[s], kind == 0 ? FIELD_POWER : FIELD_UNIT,
+                                            (kind + 1) * nfs + s * n_shells + a, -1, {0, 0, 0}});
+    }
     for (int a = 0; a < n_shells; ++a) fdu.push_back(FieldDesc{a, 0, FIELD_UNIT, a, -1, {0, 0, 0}});
     bsp_status st;
     if ((st = upload(&p->d_shell_of, shell_of)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||
@@ -538,28 +630,198 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     size_t t1, t2;
     t12_sizes(g, sizeof(float), &t1, &t2);
     const size_t nfields32 = (size_t)p->nslot() * n_shells;
-    p->fld32_bytes = round256(nfields32 * p->npts() * sizeof(float));
+    p->fld32_bytes = round256((p->shot ? 3 : 1) * nfields32 * p->npts() * sizeof(float));
     p->fb32 = (int)std::max<size_t>(1, std::min<size_t>(nfields32, (size_t)(2ull << 30) / (t1 + t2)));
+    p->fb_cap = p->fb32;
     t12_sizes(g, sizeof(double), &t1, &t2);
     p->fld64_bytes = round256((size_t)n_shells * p->npts() * sizeof(double));
     p->fb64 = (int)std::max<size_t>(1, std::min<size_t>(n_shells, (size_t)(2ull << 30) / (t1 + t2)));
     // the valid-bin schedule has at most as many works as the bound, and
     // nsplit <= ceil(target / nwork), so nwork * nsplit <= target + nwork
     p->part_bytes = round256(std::max(partial_bytes(bound, CCOLS),
-                                      (size_t)(p->target_ctas + bound.works.size()) * 64 * CCOLS * sizeof(double)));
+                                      (size_t)(4096 + bound.works.size()) * 64 * CCOLS * sizeof(double)));
+    if (p->shot) p->part_bytes *= 4;   // main sum + three shot-noise sums
     p->tout_bytes = round256(p->ells.size() * p->cand.size() * sizeof(double));
     if (p->tc) {
         p->f0_bytes = round256((size_t)n_shells * p->npts() * sizeof(float));
         p->plane_bytes = round256(nfields32 * p->npts() * 2);
-        TcSched tb = build_tc_sched(p->cand, p->out_slots, n_shells, p->npts());
-        p->tc_part_bytes = round256(std::max<size_t>((size_t)(1216 + tb.works.size()),
-                                                     tb.works.size() * (size_t)tb.nsplit) *
-                                    TC_UNIT * sizeof(double));
+        TcSched tb = build_tc_sched(p->cand, p->out_slots, n_shells, p->npts(), p->nsm);
+        p->tc_part_bytes = round256(std::max<size_t>((size_t)p->nsm, tb.units.size()) * TC_UNIT * sizeof(double));
     }
     p->cnt_out_bytes = round256(p->cand.size() * sizeof(double));
     p->ws_bytes = std::max(layout_compute(p).end, layout_counts(p).end);
     p->staging_bytes = round256((size_t)n * n * (n / 2 + 1) * 8) + p->tout_bytes;
     *out = p;
+    return BSP_OK;
+}
+
+bsp_status bsp_plan_create_modal(bsp_plan** out, int n, double box, int n_funcs, const double* radial, int n_ell,
+                                 const int* ells, int prec, unsigned flags) {
+    if (!out) return BSP_EINVAL;
+    *out = nullptr;
+    if (!good_size(n) || !(box > 0) || !std::isfinite(box) || n_funcs < 1 || n_funcs > 64 || !radial ||
+        n_ell < 1 || n_ell > 3 || !ells || flags != 0)
+        return BSP_EINVAL;
+    for (int i = 0; i < n_ell; ++i) {
+        if (ells[i] != 0 && ells[i] != 2 && ells[i] != 4) return BSP_EINVAL;
+        if (i && ells[i] <= ells[i - 1]) return BSP_EINVAL;
+    }
+    if (prec != BSP_FP32 && prec != BSP_SPLIT_BF16 && prec != BSP_BF16 && prec != BSP_SPLIT_F16)
+        return BSP_EUNSUPPORTED;
+    const int n2max = 3 * (n / 2) * (n / 2);
+    std::vector<float> tab((size_t)n_funcs * (n2max + 1));
+    int maxn2 = 0;
+    for (int f = 0; f < n_funcs; ++f)
+        for (int n2 = 0; n2 <= n2max; ++n2) {
+            const double v = radial[(size_t)f * (n2max + 1) + n2];
+            if (!std::isfinite(v)) return BSP_EINVAL;
+            tab[(size_t)f * (n2max + 1) + n2] = (float)v;
+            if (v != 0.0 && n2 > maxn2) maxn2 = n2;
+        }
+    if (maxn2 == 0) return BSP_EINVAL;
+
+    bsp_plan* p = new (std::nothrow) bsp_plan();
+    if (!p) return BSP_ENOMEM;
+    p->modal = true;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            p->nsm = sms;
+    }
+    p->n = n;
+    p->box = box;
+    p->nsh = n_funcs;
+    p->ells.assign(ells, ells + n_ell);
+    p->prec = prec;
+    p->tc = prec != BSP_FP32;
+    p->nprod = prec == BSP_BF16 ? 1 : 3;
+    p->slot_ell.push_back(0);
+    for (int l : p->ells)
+        if (l != 0) p->slot_ell.push_back(l);
+    for (int l : p->ells)
+        for (int s = 0; s < p->nslot(); ++s)
+            if (p->slot_ell[s] == l) p->out_slots.push_back(s);
+    for (int s = 0; s < p->nslot(); ++s)
+        if (p->slot_ell[s] == 2) p->slot2 = s;
+    for (int l : p->ells)
+        if (l == 4) p->need_u = true;
+    if (p->need_u && p->slot2 < 0) {
+        // the l = 4 sum needs the l = 2 fields even when l = 2 is not an output
+        p->slot_ell.push_back(2);
+        p->slot2 = p->nslot() - 1;
+    }
+    FftGeom& g = p->geom;
+    g.n = n;
+    int K = 0;
+    while ((K + 1) * (K + 1) <= maxn2) ++K;
+    if (K >= n / 2) {
+        g.K = n / 2; g.nK = n; g.pruned = 0; g.nKz = n / 2 + 1;
+    } else {
+        g.K = K; g.nK = 2 * K + 1; g.pruned = 1; g.nKz = K + 1;
+    }
+    g.n2max = n2max;
+    if (!radix_plan(n, g.rad, &g.nrad) || !radix_plan(n / 2, g.rad_h, &g.nrad_h)) {
+        delete p;
+        return BSP_EUNSUPPORTED;
+    }
+    std::vector<cx<double>> tw64(n);
+    std::vector<cx<float>> tw32(n);
+    for (int t = 0; t < n; ++t) {
+        const double ang = 2.0 * M_PI * (double)t / (double)n;
+        tw64[t] = {std::cos(ang), std::sin(ang)};
+        tw32[t] = {(float)tw64[t].re, (float)tw64[t].im};
+    }
+    // fields M^l_a = sum w_l R_a[n^2] delta e^{ik.x}; on the tensor-core path the
+    // FP32 copies are the pair factors: slot 0, then slot2 (for U) at index nf + a
+    const int nf = n_funcs;
+    std::vector<FieldDesc> fdd, fdt;
+    for (int s = 0; s < p->nslot(); ++s)
+        for (int a = 0; a < nf; ++a) {
+            const int f = s * nf + a;
+            fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_RADIAL, f, -1, {0, 0, 0}});
+            int o32 = -1;
+            if (s == 0) o32 = a;
+            else if (p->need_u && s == p->slot2) o32 = nf + a;
+            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_RADIAL, o32, f, {0, 0, 0}});
+        }
+    bsp_status st;
+    if ((st = upload(&p->d_radial, tab)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||
+        (st = upload(&p->d_tw64, tw64)) != BSP_OK || (st = upload(&p->d_fd_delta, fdd)) != BSP_OK ||
+        (st = upload(&p->d_fd_tc, fdt)) != BSP_OK || (st = upload(&p->d_err, std::vector<int>{0})) != BSP_OK ||
+        (st = upload(&p->d_ells, p->ells)) != BSP_OK ||
+        (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)(p->nslot() + 2) * nf, 0u))) != BSP_OK) {
+        delete p;
+        return st;
+    }
+    // every (a; b >= c): T^l for all slots, U on slot 0 rows
+    for (int a = 0; a < nf; ++a)
+        for (int b = 0; b < nf; ++b)
+            for (int c = 0; c <= b; ++c) p->bins.push_back({a, b, c});
+    p->counts.assign(p->bins.size(), 1.0);
+    const size_t nall = p->bins.size();
+    size_t t1, t2;
+    t12_sizes(g, sizeof(float), &t1, &t2);
+    const size_t nfields = (size_t)p->nslot() * nf;
+    p->fb32 = (int)std::max<size_t>(1, std::min<size_t>(nfields, (size_t)(2ull << 30) / (t1 + t2)));
+    p->tfull_bytes = round256(p->ells.size() * nall * sizeof(double));
+    p->ufull_bytes = p->need_u ? round256(nall * sizeof(double)) : 0;
+    if (!p->tc) {
+        p->comp_sched = build_sched(p->bins, p->out_slots, nf, p->npts(), p->target_ctas, CCOLS);
+        p->fld32_bytes = round256(nfields * p->npts() * sizeof(float));
+        p->part_bytes = round256(partial_bytes(p->comp_sched, CCOLS));
+        if ((st = upload_sched(p->comp_dev, p->comp_sched)) != BSP_OK) {
+            delete p;
+            return st;
+        }
+        if (p->need_u) {
+            p->u_sched = build_sched(p->bins, std::vector<int>{0}, nf, p->npts(), p->target_ctas, CCOLS);
+            p->upart_bytes = round256(partial_bytes(p->u_sched, CCOLS));
+            if ((st = upload_sched(p->u_dev, p->u_sched)) != BSP_OK) {
+                delete p;
+                return st;
+            }
+        }
+    } else {
+        p->tc_sched = build_tc_sched(p->bins, p->out_slots, nf, p->npts(), p->nsm);
+        p->f0_bytes = round256((p->need_u ? 2 : 1) * (size_t)nf * p->npts() * sizeof(float));
+        p->plane_bytes = round256(nfields * p->npts() * 2);
+        p->tc_part_bytes = round256(p->tc_sched.units.size() * TC_UNIT * sizeof(double));
+        if ((st = upload(&p->d_tc_units, p->tc_sched.units)) != BSP_OK ||
+            (st = upload(&p->d_tc_works, p->tc_sched.works)) != BSP_OK ||
+            (st = upload(&p->d_tc_pairs, p->tc_sched.pairs)) != BSP_OK ||
+            (st = upload(&p->d_tc_loc, p->tc_sched.loc)) != BSP_OK) {
+            delete p;
+            return st;
+        }
+        if (p->need_u) {
+            p->tc_u_sched = build_tc_sched(p->bins, std::vector<int>{0}, nf, p->npts(), p->nsm);
+            p->tcu_part_bytes = round256(p->tc_u_sched.units.size() * TC_UNIT * sizeof(double));
+            if ((st = upload(&p->d_tcu_units, p->tc_u_sched.units)) != BSP_OK ||
+                (st = upload(&p->d_tcu_works, p->tc_u_sched.works)) != BSP_OK ||
+                (st = upload(&p->d_tcu_pairs, p->tc_u_sched.pairs)) != BSP_OK ||
+                (st = upload(&p->d_tcu_loc, p->tc_u_sched.loc)) != BSP_OK) {
+                delete p;
+                return st;
+            }
+        }
+    }
+    if ((st = upload(&p->d_counts, p->counts)) != BSP_OK) {
+        delete p;
+        return st;
+    }
+    p->have_counts = true;
+    p->ws_bytes = layout_compute(p).end;
+    p->staging_bytes = 0;
+    *out = p;
+    return BSP_OK;
+}
+
+bsp_status bsp_modal_size(const bsp_plan* p, int* n_funcs, int* n_trip) {
+    if (!p || !p->modal) return BSP_EINVAL;
+    const int nf = p->nsh;
+    if (n_funcs) *n_funcs = nf;
+    if (n_trip) *n_trip = nf * (nf + 1) * (nf + 2) / 6;
     return BSP_OK;
 }
 
@@ -581,16 +843,15 @@ bsp_status bsp_host_staging_size(const bsp_plan* p, size_t* bytes) {
 // device copy of the counts.
 static bsp_status finish_counts(bsp_plan* p) {
     p->comp_sched = build_sched(p->bins, p->out_slots, p->nsh, p->npts(), p->target_ctas, CCOLS);
-    if (round256(partial_bytes(p->comp_sched, CCOLS)) > p->part_bytes) return BSP_ENOMEM;
+    if (round256(partial_bytes(p->comp_sched, CCOLS)) * (p->shot ? 4 : 1) > p->part_bytes) return BSP_ENOMEM;
     bsp_status s = upload_sched(p->comp_dev, p->comp_sched);
     if (s != BSP_OK) return s;
     if (p->tc) {
-        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->nsh, p->npts());
-        if (round256(p->tc_sched.works.size() * (size_t)p->tc_sched.nsplit * TC_UNIT * sizeof(double)) >
-            p->tc_part_bytes)
-            return BSP_ENOMEM;
-        cudaFree(p->d_tc_works); cudaFree(p->d_tc_pairs); cudaFree(p->d_tc_loc);
-        p->d_tc_works = nullptr; p->d_tc_pairs = nullptr; p->d_tc_loc = nullptr;
+        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->nsh, p->npts(), p->nsm);
+        if (round256(p->tc_sched.units.size() * TC_UNIT * sizeof(double)) > p->tc_part_bytes) return BSP_ENOMEM;
+        cudaFree(p->d_tc_works); cudaFree(p->d_tc_pairs); cudaFree(p->d_tc_loc); cudaFree(p->d_tc_units);
+        p->d_tc_works = nullptr; p->d_tc_pairs = nullptr; p->d_tc_loc = nullptr; p->d_tc_units = nullptr;
+        if ((s = upload(&p->d_tc_units, p->tc_sched.units)) != BSP_OK) return s;
         if ((s = upload(&p->d_tc_works, p->tc_sched.works)) != BSP_OK) return s;
         if ((s = upload(&p->d_tc_pairs, p->tc_sched.pairs)) != BSP_OK) return s;
         if ((s = upload(&p->d_tc_loc, p->tc_sched.loc)) != BSP_OK) return s;
@@ -603,7 +864,7 @@ static bsp_status finish_counts(bsp_plan* p) {
 }
 
 bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
-    if (!p || !ws || !aligned256(ws)) return BSP_EINVAL;
+    if (!p || !ws || !aligned256(ws) || p->modal) return BSP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const Layout L = layout_counts(p);
     char* base = (char*)ws;
@@ -622,7 +883,7 @@ bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
     }
     double* partial = (double*)(base + L.partial);
     double* cnt = (double*)(base + L.cnt);
-    cudaError_t e = launch_contract_cc<double>(f64, p->npts(), p->cand_dev.works, p->cand_dev.nwork,
+    cudaError_t e = launch_contract_cc<double>(f64, f64, nullptr, 0, p->npts(), p->cand_dev.works, p->cand_dev.nwork,
                                                p->cand_dev.pairs, p->cand_dev.rowf, p->npts(),
                                                p->cand_dev.nsplit, partial, st);
     if (e != cudaSuccess) return cuda_fail(e, "contract (counts)");
@@ -679,7 +940,7 @@ static bsp_status mark(bsp_plan* p, cudaStream_t st, int k) {
 
 static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, void* ws, cudaStream_t st,
                                double* B) {
-    if (nbar != 0.0) return BSP_EUNSUPPORTED;
+    if (nbar != 0.0 && !p->shot) return p->tc ? BSP_EUNSUPPORTED : BSP_EINVAL;
     if (p->profiling && p->ev_used % 4 != 0) return BSP_ESTATE;
     bsp_status ms;
     if ((ms = mark(p, st, 0)) != BSP_OK) return ms;
@@ -694,7 +955,6 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
         cx<float>* t2 = (cx<float>*)(base + L.t2);
         const int nf = p->nslot() * p->nsh;
         unsigned* fmax2 = p->d_fmax;              // [nf]  max |T2| per field (bounds |F|)
-        unsigned* f0max = p->d_fmax + nf;         // [nsh] exact max |F0| per shell
         CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * (nf + p->nsh), st));
         CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st));
         const int f16 = p->prec == BSP_SPLIT_F16 ? 1 : 0;
@@ -702,7 +962,7 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
             int nb = std::min(p->fb32, nf - f0i);
             cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, p->d_shell_of, nullptr,
                                                      p->d_fd_tc + f0i, nb, p->d_tw32, t1, t2, f0, p->npts(), hi,
-                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, f0max, st);
+                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, nullptr, st);
             if (e != cudaSuccess) return cuda_fail(e, "fft");
             launches += 3;
         }
@@ -716,14 +976,14 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
             return es;
         double* partial = (double*)(base + L.partial);
         double* tout = (double*)(base + L.tout);
-        cudaError_t e = launch_contract_tc(f16 != 0, &tmf0, &tmhi, &tmlo, p->d_tc_works,
-                                           (int)p->tc_sched.works.size(), p->d_tc_pairs, f0max, fmax2,
-                                           2.f * (float)p->geom.nKz, p->npts(), p->tc_sched.nsplit, p->nprod,
+        cudaError_t e = launch_contract_tc(f16 != 0, &tmf0, &tmhi, &tmlo, p->d_tc_works, p->d_tc_units,
+                                           (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
+                                           p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
                                            p->chunk_kb, partial, p->d_err, st);
         if (e != cudaSuccess) return cuda_fail(e, "contract (tensor cores)");
         if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
         const double V = p->box * p->box * p->box;
-        e = launch_reduce(partial, p->tc_sched.nsplit, TC_UNIT, 128, p->d_tc_loc, (int)p->tc_sched.loc.size(),
+        e = launch_reduce(partial, 0, TC_UNIT, 128, p->d_tc_loc, (int)p->tc_sched.loc.size(),
                           (int)p->bins.size(), p->d_counts, 1.0 / (V * (double)p->npts()), 1, tout, B, st);
         if (e != cudaSuccess) return cuda_fail(e, "reduce");
         if ((ms = mark(p, st, 3)) != BSP_OK) return ms;
@@ -734,8 +994,10 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
     cx<float>* t1 = (cx<float>*)(base + L.t1);
     cx<float>* t2 = (cx<float>*)(base + L.t2);
     const int nf = p->nslot() * p->nsh;
-    for (int f0 = 0; f0 < nf; f0 += p->fb32) {
-        int nb = std::min(p->fb32, nf - f0);
+    const bool shot = nbar > 0.0;
+    const int nft = shot ? 3 * nf : nf;   // F, then S and W with shot noise
+    for (int f0 = 0; f0 < nft; f0 += p->fb32) {
+        int nb = std::min(p->fb32, nft - f0);
         cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, p->d_shell_of, nullptr,
                                                  p->d_fd_delta + f0, nb, p->d_tw32, t1, t2, f32, p->npts(), nullptr,
                                                  nullptr, 0, nullptr, nullptr, st);
@@ -745,21 +1007,163 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
     if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
     double* partial = (double*)(base + L.partial);
     double* tout = (double*)(base + L.tout);
-    cudaError_t e = launch_contract_cc<float>(f32, p->npts(), p->comp_dev.works, p->comp_dev.nwork,
-                                              p->comp_dev.pairs, p->comp_dev.rowf, p->npts(),
-                                              p->comp_dev.nsplit, partial, st);
-    if (e != cudaSuccess) return cuda_fail(e, "contract");
+    const size_t pstride = round256(partial_bytes(p->comp_sched, CCOLS)) / sizeof(double);
+    const size_t fs = (size_t)nf * p->npts();
+    const float* F = f32;
+    const float* S = f32 + fs;
+    const float* W = f32 + 2 * fs;   // slot 0 of W: the unit fields I
+    struct Job { const float *rows, *px, *py; int sym; };
+    Job jobs[4] = {{F, F, nullptr, 0},      // T: rows F^l_a, pairs F_b F_c
+                   {S, W, nullptr, 0},      // rows S^l_a (w_l |delta|^2), pairs I_b I_c
+                   {W, S, W, 1},            // rows W^l_a, pairs S_b I_c + I_b S_c
+                   {W, W, nullptr, 0}};     // rows W^l_a, pairs I_b I_c
+    for (int j = 0; j < (shot ? 4 : 1); ++j) {
+        cudaError_t e = launch_contract_cc<float>(jobs[j].rows, jobs[j].px, jobs[j].py, jobs[j].sym, p->npts(),
+                                                  p->comp_dev.works, p->comp_dev.nwork, p->comp_dev.pairs,
+                                                  p->comp_dev.rowf, p->npts(), p->comp_dev.nsplit,
+                                                  partial + j * pstride, st);
+        if (e != cudaSuccess) return cuda_fail(e, "contract");
+        ++launches;
+    }
     if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
-    const double V = p->box * p->box * p->box;
-    e = launch_reduce(partial, p->comp_dev.nsplit, 0, 0, p->comp_dev.loc, p->comp_dev.nloc, (int)p->bins.size(),
-                      p->d_counts, 1.0 / (V * (double)p->npts()), 1, tout, B, st);
+    const double V = p->box * p->box * p->box, n3 = (double)p->npts();
+    // B = [T / V - (T_S + T_SI) / (V nbar) + 2 T_W / nbar^2] / (n^3 N_abc)   (Poisson shot noise)
+    ShotTerms sh{};
+    if (shot) {
+        sh.n = 3;
+        sh.partial[0] = partial + pstride;
+        sh.partial[1] = partial + 2 * pstride;
+        sh.partial[2] = partial + 3 * pstride;
+        sh.coef[0] = 1.0 / (V * nbar * n3);
+        sh.coef[1] = 1.0 / (V * nbar * n3);
+        sh.coef[2] = -2.0 / (nbar * nbar * n3);
+    }
+    cudaError_t e = launch_reduce(partial, p->comp_dev.nsplit, 0, 0, p->comp_dev.loc, p->comp_dev.nloc,
+                                  (int)p->bins.size(), p->d_counts, 1.0 / (V * n3), 1, tout, B, st,
+                                  shot ? &sh : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "reduce");
     if ((ms = mark(p, st, 3)) != BSP_OK) return ms;
-    p->launches_last = launches + 2;
+    p->launches_last = launches + 1;
+    return BSP_OK;
+}
+
+bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* stream, double* S) {
+    if (!p || !p->modal || !delta_k || !ws || !S || !aligned256(delta_k) || !aligned256(ws) || !aligned256(S))
+        return BSP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Layout L = layout_compute(p);
+    char* base = (char*)ws;
+    const int nf = p->nsh, nfields = p->nslot() * nf;
+    const size_t nall = p->bins.size();
+    const int ntrip = nf * (nf + 1) * (nf + 2) / 6;
+    double* tfull = (double*)(base + L.tout);
+    double* ufull = p->need_u ? (double*)(base + L.tout + p->tfull_bytes) : nullptr;
+    const double V = p->box * p->box * p->box, n3 = (double)p->npts();
+    bsp_status ms;
+    if ((ms = mark(p, st, 0)) != BSP_OK) return ms;
+    int launches = 0;
+    if (!p->tc) {
+        float* f32 = (float*)(base + L.fields);
+        cx<float>* t1 = (cx<float>*)(base + L.t1);
+        cx<float>* t2 = (cx<float>*)(base + L.t2);
+        for (int f0 = 0; f0 < nfields; f0 += p->fb32) {
+            const int nb = std::min(p->fb32, nfields - f0);
+            cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, nullptr, p->d_radial,
+                                                     p->d_fd_delta + f0, nb, p->d_tw32, t1, t2, f32, p->npts(),
+                                                     nullptr, nullptr, 0, nullptr, nullptr, st);
+            if (e != cudaSuccess) return cuda_fail(e, "fft (modal)");
+            launches += 3;
+        }
+        if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
+        double* part = (double*)(base + L.partial);
+        cudaError_t e = launch_contract_cc<float>(f32, f32, nullptr, 0, p->npts(), p->comp_dev.works,
+                                                  p->comp_dev.nwork, p->comp_dev.pairs, p->comp_dev.rowf,
+                                                  p->npts(), p->comp_dev.nsplit, part, st);
+        if (e != cudaSuccess) return cuda_fail(e, "contract (modal)");
+        ++launches;
+        if (p->need_u) {
+            const float* m2 = f32 + (size_t)p->slot2 * nf * p->npts();
+            e = launch_contract_cc<float>(f32, m2, nullptr, 0, p->npts(), p->u_dev.works, p->u_dev.nwork,
+                                          p->u_dev.pairs, p->u_dev.rowf, p->npts(), p->u_dev.nsplit,
+                                          part + p->part_bytes / sizeof(double), st);
+            if (e != cudaSuccess) return cuda_fail(e, "contract (modal U)");
+            ++launches;
+        }
+        if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
+        e = launch_reduce(part, p->comp_dev.nsplit, 0, 0, p->comp_dev.loc, p->comp_dev.nloc, (int)nall,
+                          p->d_counts, 1.0, 2, nullptr, tfull, st);
+        if (e == cudaSuccess && p->need_u)
+            e = launch_reduce(part + p->part_bytes / sizeof(double), p->u_dev.nsplit, 0, 0, p->u_dev.loc,
+                              p->u_dev.nloc, (int)nall, p->d_counts, 1.0, 2, nullptr, ufull, st);
+        if (e != cudaSuccess) return cuda_fail(e, "reduce (modal)");
+        launches += p->need_u ? 2 : 1;
+    } else {
+        float* f0 = (float*)(base + L.fields);
+        uint32_t* hi = (uint32_t*)(base + L.fields + p->f0_bytes);
+        uint32_t* lo = (uint32_t*)(base + L.fields + p->f0_bytes + p->plane_bytes);
+        cx<float>* t1 = (cx<float>*)(base + L.t1);
+        cx<float>* t2 = (cx<float>*)(base + L.t2);
+        unsigned* fmax2 = p->d_fmax;                    // [nfields] max |T2| per field (bounds |F|)
+        CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * (nfields + 2 * nf), st));
+        CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st));
+        const int f16 = p->prec == BSP_SPLIT_F16 ? 1 : 0;
+        for (int fi = 0; fi < nfields; fi += p->fb32) {
+            const int nb = std::min(p->fb32, nfields - fi);
+            cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, nullptr, p->d_radial,
+                                                     p->d_fd_tc + fi, nb, p->d_tw32, t1, t2, f0, p->npts(), hi,
+                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, nullptr, st);
+            if (e != cudaSuccess) return cuda_fail(e, "fft (modal)");
+            launches += 3;
+        }
+        if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
+        const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        CUtensorMap tmf0, tmf2, tmhi, tmlo;
+        bsp_status es;
+        if ((es = encode_map(&tmf0, f0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nf, p->npts(), false)) != BSP_OK ||
+            (es = encode_map(&tmhi, hi, t16, 2, nfields, p->npts(), true)) != BSP_OK ||
+            (es = encode_map(&tmlo, p->nprod == 3 ? (void*)lo : (void*)hi, t16, 2, nfields, p->npts(), true)) !=
+                BSP_OK)
+            return es;
+        if (p->need_u &&
+            (es = encode_map(&tmf2, f0 + (size_t)nf * p->npts(), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nf, p->npts(),
+                             false)) != BSP_OK)
+            return es;
+        double* part = (double*)(base + L.partial);
+        double* upart = (double*)(base + L.partial + p->tc_part_bytes);
+        cudaError_t e = launch_contract_tc(f16 != 0, &tmf0, &tmhi, &tmlo, p->d_tc_works, p->d_tc_units,
+                                           (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
+                                           p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
+                                           p->chunk_kb, part, p->d_err, st);
+        if (e != cudaSuccess) return cuda_fail(e, "contract (modal, tensor cores)");
+        ++launches;
+        if (p->need_u) {
+            e = launch_contract_tc(f16 != 0, &tmf2, &tmhi, &tmlo, p->d_tcu_works, p->d_tcu_units,
+                                   (int)p->tc_u_sched.units.size(), p->tc_u_sched.lsup, p->tc_u_sched.nsup,
+                                   p->d_tcu_pairs, p->slot2 * nf, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
+                                   p->chunk_kb, upart, p->d_err, st);
+            if (e != cudaSuccess) return cuda_fail(e, "contract (modal U, tensor cores)");
+            ++launches;
+        }
+        if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
+        e = launch_reduce(part, 0, TC_UNIT, 128, p->d_tc_loc, (int)p->tc_sched.loc.size(),
+                          (int)nall, p->d_counts, 1.0, 2, nullptr, tfull, st);
+        if (e == cudaSuccess && p->need_u)
+            e = launch_reduce(upart, 0, TC_UNIT, 128, p->d_tcu_loc,
+                              (int)p->tc_u_sched.loc.size(), (int)nall, p->d_counts, 1.0, 2, nullptr, ufull, st);
+        if (e != cudaSuccess) return cuda_fail(e, "reduce (modal)");
+        launches += p->need_u ? 2 : 1;
+    }
+    // <<B_l | Q_pqr>> = S / (n^3 V^3)
+    cudaError_t e = launch_modal_assemble(tfull, ufull, p->d_ells, (int)p->ells.size(), nf, (long long)nall, ntrip,
+                                          1.0 / (n3 * V * V * V), S, st);
+    if (e != cudaSuccess) return cuda_fail(e, "assemble (modal)");
+    if ((ms = mark(p, st, 3)) != BSP_OK) return ms;
+    p->launches_last = launches + 1;
     return BSP_OK;
 }
 
 bsp_status bsp_compute(bsp_plan* p, const void* delta_k, double nbar, void* ws, void* stream, double* B) {
+    if (p && p->modal) return BSP_EINVAL;
     if (!p || !delta_k || !ws || !B || !aligned256(delta_k) || !aligned256(ws) || !aligned256(B) ||
         !(nbar >= 0) || !std::isfinite(nbar))
         return BSP_EINVAL;
@@ -798,7 +1202,7 @@ bsp_status bsp_plan_stats(const bsp_plan* p, double* st) {
     if (p->tc) {
         for (const TcWork& w : p->tc_sched.works) issued += 128.0 * w.n * p->nprod;
         works = (double)p->tc_sched.works.size();
-        nsplit = p->tc_sched.nsplit;
+        nsplit = (double)p->tc_sched.units.size();
     } else {
         issued = (double)p->comp_sched.works.size() * 64.0 * 64.0;
         works = (double)p->comp_sched.works.size();
@@ -808,6 +1212,16 @@ bsp_status bsp_plan_stats(const bsp_plan* p, double* st) {
     st[1] = (double)p->ells.size() * p->bins.size();
     st[2] = works;
     st[3] = nsplit;
+    return BSP_OK;
+}
+
+bsp_status bsp_plan_tune(bsp_plan* p, int target_ctas, int fft_batch) {
+    if (!p || target_ctas < 0 || fft_batch < 0 || target_ctas > 4096) return BSP_EINVAL;
+    if (fft_batch > 0) p->fb32 = std::min(fft_batch, p->fb_cap);
+    if (target_ctas > 0 && target_ctas != p->target_ctas) {
+        p->target_ctas = target_ctas;
+        if (p->have_counts && !p->modal) return finish_counts(p);
+    }
     return BSP_OK;
 }
 

@@ -58,8 +58,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
+// rows: row fields (row_fields[] index them from `rows`); the pair product of
+// pair (b, c) is X_b Y_c, or X_b Y_c + Y_b X_c with `sym`, X = px + s fstride.
 template <typename R>
-__global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict__ fields, size_t fstride,
+__global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict__ rows, const R* __restrict__ px,
+                                                            const R* __restrict__ py, int sym, size_t fstride,
                                                             const Work* __restrict__ works,
                                                             const int2* __restrict__ pair_fields,
                                                             const int* __restrict__ row_fields,
@@ -73,6 +76,8 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
     __shared__ __align__(16) R As[XC][AS];
     __shared__ __align__(16) R Ps[XC][PS];
     __shared__ __align__(16) R Fz[64][XC];
+    __shared__ __align__(16) R Fy[64][XC];
+    const bool two = py != px;
     __shared__ int2 pf[CC_COLS];
     __shared__ int rf[CC_ROWS];
 
@@ -106,18 +111,26 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
         const int nx = (int)min((size_t)XC, x_end - x0);
         for (int e = tid; e < w.nshell * XC; e += CC_THREADS) {
             const int s = e / XC, x = e % XC;
-            Fz[s][x] = x < nx ? fields[(size_t)(w.shell_lo + s) * fstride + x0 + x] : (R)0;
+            const size_t o = (size_t)(w.shell_lo + s) * fstride + x0 + x;
+            Fz[s][x] = x < nx ? px[o] : (R)0;
+            if (two) Fy[s][x] = x < nx ? py[o] : (R)0;
         }
         for (int e = tid; e < CC_ROWS * XC; e += CC_THREADS) {
             const int r = e / XC, x = e % XC;
             const int f = rf[r];
-            As[x][r] = (f >= 0 && x < nx) ? fields[(size_t)f * fstride + x0 + x] : (R)0;
+            As[x][r] = (f >= 0 && x < nx) ? rows[(size_t)f * fstride + x0 + x] : (R)0;
         }
         __syncthreads();
         for (int e = tid; e < CC_COLS * XC; e += CC_THREADS) {
             const int p = e % CC_COLS, x = e / CC_COLS;
             const int2 bc = pf[p];
-            Ps[x][p] = bc.x >= 0 ? Fz[bc.x][x] * Fz[bc.y][x] : (R)0;
+            R v = (R)0;
+            if (bc.x >= 0) {
+                if (!two) v = Fz[bc.x][x] * Fz[bc.y][x];
+                else if (!sym) v = Fz[bc.x][x] * Fy[bc.y][x];
+                else v = Fz[bc.x][x] * Fy[bc.y][x] + Fy[bc.x][x] * Fz[bc.y][x];
+            }
+            Ps[x][p] = v;
         }
         __syncthreads();
 #pragma unroll 4
@@ -156,46 +169,68 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
 
 __global__ void k_reduce(const double* __restrict__ partial, int nsplit, size_t unit, int row_stride,
                          const BinLoc* __restrict__ loc, int nout, int nbins, const double* __restrict__ counts,
-                         double scale, int mode, double* __restrict__ T_out, double* __restrict__ out) {
+                         double scale, int mode, double* __restrict__ T_out, double* __restrict__ out,
+                         ShotTerms shot) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nout) return;
     const BinLoc L = loc[i];
-    const double* p = partial + (size_t)L.work * nsplit * unit + (size_t)L.row * row_stride + L.col;
+    // nsplit > 0: slots work*nsplit .. +nsplit; else slots L.work .. L.work + L.pad
+    const int nsum = nsplit > 0 ? nsplit : L.pad;
+    const size_t off = (size_t)L.work * (nsplit > 0 ? nsplit : 1) * unit + (size_t)L.row * row_stride + L.col;
     double s = 0.0;
-    for (int k = 0; k < nsplit; ++k) s += p[(size_t)k * unit];
+    for (int k = 0; k < nsum; ++k) s += partial[off + (size_t)k * unit];
     if (T_out) T_out[i] = s;
-    if (mode == 0) out[i] = rint(s * scale);
-    else out[i] = s * scale / counts[i % nbins];
+    if (mode == 0) {
+        out[i] = rint(s * scale);
+        return;
+    }
+    if (mode == 2) {   // raw sums, scaled
+        out[i] = s * scale;
+        return;
+    }
+    double v = s * scale;
+    if (shot.n > 0) {
+        // sum over the partial sets of the shot-noise contractions, each in a fixed order
+        for (int t = 0; t < shot.n; ++t) {
+            double u = 0.0;
+            for (int k = 0; k < nsum; ++k) u += shot.partial[t][off + (size_t)k * unit];
+            v -= shot.coef[t] * u;
+        }
+    }
+    out[i] = v / counts[i % nbins];
 }
 
 }  // namespace
 
 template <typename R>
-cudaError_t launch_contract_cc(const R* fields, size_t fstride, const Work* works, int nwork,
-                               const int2* pair_fields, const int* row_fields, size_t npts, int nsplit,
+cudaError_t launch_contract_cc(const R* rows, const R* px, const R* py, int sym, size_t fstride, const Work* works,
+                               int nwork, const int2* pair_fields, const int* row_fields, size_t npts, int nsplit,
                                double* partial, cudaStream_t st) {
     constexpr int XC = CCCfg<R>::XC;
     size_t seg = (npts + nsplit - 1) / nsplit;
     seg = (seg + XC - 1) / XC * XC;
     dim3 grid(nwork, nsplit);
-    k_contract_cc<R><<<grid, CC_THREADS, 0, st>>>(fields, fstride, works, pair_fields, row_fields, npts, seg,
-                                                  partial);
+    k_contract_cc<R><<<grid, CC_THREADS, 0, st>>>(rows, px, py ? py : px, sym, fstride, works, pair_fields,
+                                                  row_fields, npts, seg, partial);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_contract_cc<float>(const float*, size_t, const Work*, int, const int2*, const int*,
-                                               size_t, int, double*, cudaStream_t);
-template cudaError_t launch_contract_cc<double>(const double*, size_t, const Work*, int, const int2*,
-                                                const int*, size_t, int, double*, cudaStream_t);
+template cudaError_t launch_contract_cc<float>(const float*, const float*, const float*, int, size_t, const Work*,
+                                               int, const int2*, const int*, size_t, int, double*, cudaStream_t);
+template cudaError_t launch_contract_cc<double>(const double*, const double*, const double*, int, size_t,
+                                                const Work*, int, const int2*, const int*, size_t, int, double*,
+                                                cudaStream_t);
 
 cudaError_t launch_reduce(const double* partial, int nsplit, size_t unit, int row_stride, const BinLoc* loc,
                           int nout, int nbins, const double* counts, double scale, int mode, double* T_out,
-                          double* out, cudaStream_t st) {
+                          double* out, cudaStream_t st, const ShotTerms* shot) {
+    ShotTerms none{};
+    none.n = 0;
     if (nout <= 0) return cudaSuccess;
     if (unit == 0) unit = CC_OUT;
     if (row_stride == 0) row_stride = CC_COLS;
     k_reduce<<<(nout + 255) / 256, 256, 0, st>>>(partial, nsplit, unit, row_stride, loc, nout, nbins, counts, scale,
-                                                 mode, T_out, out);
+                                                 mode, T_out, out, shot ? *shot : none);
     return cudaGetLastError();
 }
 

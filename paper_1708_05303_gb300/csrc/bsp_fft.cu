@@ -74,6 +74,27 @@ __device__ __forceinline__ void butterfly(cx<R>* v) {
         v[6] = csub(e[2], w2o);
         v[3] = cadd(e[3], w3o);
         v[7] = csub(e[3], w3o);
+    } else if constexpr (RADIX == 16) {
+        // 16 = 4 x 4: X[k1 + 4 k2] = sum_j2 W4^{j2 k2} W16^{j2 k1} sum_j1 x[j2 + 4 j1] W4^{j1 k1}
+        const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173;   // cos, sin 2pi/16
+        const R h = (R)0.70710678118654752440;
+        const cx<R> w[10] = {{(R)1, (R)0}, {c1, s1}, {h, h}, {s1, c1}, {(R)0, (R)1},
+                             {-s1, c1}, {-h, h}, {-c1, s1}, {(R)-1, (R)0}, {-c1, -s1}};   // W16^m, m = 0..9
+        cx<R> a[4][4];
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) {
+            cx<R> t[4] = {v[j2], v[j2 + 4], v[j2 + 8], v[j2 + 12]};
+            butterfly<R, 4>(t);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) a[j2][k1] = (j2 * k1 == 0) ? t[k1] : cmul(t[k1], w[j2 * k1]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            cx<R> u[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+            butterfly<R, 4>(u);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = u[k2];
+        }
     } else if constexpr (RADIX == 3) {
         const R s3 = (R)0.86602540378443864676;  // sqrt(3)/2
         cx<R> t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
@@ -159,8 +180,9 @@ __device__ cx<R>* fft_pingpong(cx<R>* a, cx<R>* b, int M, const int* rad, int nr
     return a;
 }
 
-// Compile-time radix list: 8s first, then 4 / 4x4 / 2 for the leftover
-// power of two, then 3s and 5s (the host's plan for the runtime path is the same).
+// Compile-time radix list: 16s for the power of two (with one 8 and/or 4 for
+// the leftover; 2^9 = 16 x 8 x 4), then 3s and 5s.  The host's plan for the
+// run-time kernels uses radices up to 8; both give the same transform.
 struct RadixList {
     int n;
     int r[8];
@@ -169,15 +191,13 @@ __host__ __device__ constexpr RadixList radix_list(int m) {
     RadixList L{0, {0, 0, 0, 0, 0, 0, 0, 0}};
     int a = 0;
     while (m % 2 == 0) { m /= 2; ++a; }
-    int n8 = a / 3, rem = a % 3;
-    int n44 = 0, n2 = 0, n4 = 0;
-    if (rem == 1 && n8 > 0) { --n8; n44 = 1; }
-    else if (rem == 1) n2 = 1;
-    else if (rem == 2) n4 = 1;
-    for (int i = 0; i < n8; ++i) L.r[L.n++] = 8;
-    if (n44) { L.r[L.n++] = 4; L.r[L.n++] = 4; }
-    if (n2) L.r[L.n++] = 2;
-    if (n4) L.r[L.n++] = 4;
+    int n16 = a / 4, rem = a % 4;
+    if (rem == 1 && n16 > 0) { --n16; }
+    for (int i = 0; i < n16; ++i) L.r[L.n++] = 16;
+    if (rem == 3) L.r[L.n++] = 8;
+    else if (rem == 2) L.r[L.n++] = 4;
+    else if (rem == 1 && a >= 5) { L.r[L.n++] = 8; L.r[L.n++] = 4; }
+    else if (rem == 1) L.r[L.n++] = 2;
     while (m % 3 == 0) { m /= 3; L.r[L.n++] = 3; }
     while (m % 5 == 0) { m /= 5; L.r[L.n++] = 5; }
     return L;
@@ -244,7 +264,15 @@ __global__ void __launch_bounds__(NTHR) k_pass1(FftGeom g, const cx<float>* __re
                 } else {
                     const cx<float> d = delta[((size_t)ix * N + iy) * (N / 2 + 1) + kz];
                     if (fd.kind == FIELD_POWER) {
-                        val.re = w * ((R)d.re * (R)d.re + (R)d.im * (R)d.im);
+                        // |delta|^2 of the Hermitian part: on the n_z = 0 and n/2 planes the
+                        // half spectrum holds both n and -n, (delta(n) + conj delta(-n)) / 2
+                        R re = (R)d.re, im = (R)d.im;
+                        if (kz == 0 || kz == N / 2) {
+                            const cx<float> m = delta[((size_t)((N - ix) % N) * N + (N - iy) % N) * (N / 2 + 1) + kz];
+                            re = (R)0.5 * (re + (R)m.re);
+                            im = (R)0.5 * (im - (R)m.im);
+                        }
+                        val.re = w * (re * re + im * im);
                     } else {
                         val.re = w * (R)d.re;
                         val.im = w * (R)d.im;
@@ -272,13 +300,14 @@ __device__ __forceinline__ void block_max_to(unsigned* dst, float m) {
     if ((threadIdx.x & 31) == 0) atomicMax(dst, __float_as_uint(m));
 }
 
-// Power of two s with bound * s in [2^14, 2^15): scaled values stay below the
-// FP16 maximum.  Exact, so dividing by s afterwards is exact.
-__device__ __forceinline__ float pow2_scale(float bound) {
+// Power of two s with bound * s in [2^(t-1), 2^t): t = 15 keeps 16-bit
+// values below the FP16 maximum; t = 7 keeps a product of two scaled pair
+// factors below 2^14.  Exact, so dividing by s afterwards is exact.
+__device__ __forceinline__ float pow2_scale(float bound, int t = 15) {
     if (!(bound > 0.f)) return 1.f;
     int e;
     frexpf(bound, &e);
-    return ldexpf(1.f, 15 - e);
+    return ldexpf(1.f, t - e);
 }
 
 template <typename R, int P, int NN>
@@ -373,7 +402,10 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
     uint32_t* dlo = (fd.out16 >= 0 && lo) ? lo + (size_t)fd.out16 * plane : nullptr;
     // |F(x,y,z)| <= sum_kz 2 |H_kz| <= 2 nKz max|T2|: the split planes are
     // scaled by the power of two that keeps that bound below 2^15
-    const float sc = (dhi && fmax2) ? pow2_scale(2.f * (float)g.nKz * __uint_as_float(fmax2[fd.out16])) : 1.f;
+    const float bound = fmax2 && fd.out16 >= 0 ? 2.f * (float)g.nKz * __uint_as_float(fmax2[fd.out16]) : 0.f;
+    const float sc = (dhi && fmax2) ? pow2_scale(bound) : 1.f;
+    // FP32 pair factors of the tensor-core path are stored pre-scaled (|F s7| < 2^7)
+    const R s7 = fmax2 ? (R)pow2_scale(bound, 7) : (R)1;
     float mx = 0.f;
     for (int e = threadIdx.x; e < M * P; e += NTHR) {
         const int m = e % M, p = e / M, y = y0 + p;
@@ -381,8 +413,8 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
         const size_t pos = ((size_t)x * N + y) * M + m;
         const cx<R> v = res[sidx<false, P>(p, m, M)];
         if (dst) {
-            reinterpret_cast<cx<R>*>(dst)[pos] = v;
-            mx = fmaxf(mx, fmaxf(fabsf((float)v.re), fabsf((float)v.im)));
+            reinterpret_cast<cx<R>*>(dst)[pos] = cx<R>{v.re * s7, v.im * s7};
+            if (f0max) mx = fmaxf(mx, fmaxf(fabsf((float)v.re), fabsf((float)v.im)));
         }
         if (dhi) {
             // two consecutive z values -> 16-bit hi and lo planes (x0 in the low half)
@@ -431,16 +463,24 @@ cudaError_t launch_n(const FftGeom& g, const cx<float>* delta, const int16_t* sh
     const size_t t2_stride = (size_t)N * N * g.nKz;
     const size_t sm12 = sizeof(cx<R>) * ((size_t)N + 2 * (size_t)smem_elems<true, C::P>(N));
     const size_t sm3 = sizeof(cx<R>) * ((size_t)N + 2 * (size_t)smem_elems<false, C::P3>(M));
+    // raise the dynamic shared-memory limit once per size (never inside a graph capture)
+    static size_t set12 = 0, set3 = 0;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_pass1<R, C::P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm12)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_pass2<R, C::P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm12)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_pass3<R, C::P3, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)) !=
-        cudaSuccess)
-        return e;
+    if (sm12 > set12) {
+        if ((e = cudaFuncSetAttribute(k_pass1<R, C::P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm12)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k_pass2<R, C::P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm12)) != cudaSuccess)
+            return e;
+        set12 = sm12;
+    }
+    if (sm3 > set3) {
+        if ((e = cudaFuncSetAttribute(k_pass3<R, C::P3, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm3)) != cudaSuccess)
+            return e;
+        set3 = sm3;
+    }
     const int nkzb = (g.nKz + C::P - 1) / C::P;
     dim3 g1(g.nK * nkzb, nfields), g2(N * nkzb, nfields), g3(N * ((N + C::P3 - 1) / C::P3), nfields);
     k_pass1<R, C::P, NN><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);

@@ -68,11 +68,21 @@ struct TcWork {
     int box_field[16];      // first field row of each box
 };
 
-struct BinLoc {   // where T of (l, bin) lives in the partial buffer
+// One persistent tensor-core CTA: the x-range is swept in super-segments of
+// `lsup` K-blocks in the same order by every CTA; this CTA handles K-blocks
+// [start, start + len) of each super-segment for work item `work`.
+struct TcUnit {
     int work;
+    int start;
+    int len;
+    int pad;
+};
+
+struct BinLoc {   // where T of (l, bin) lives in the partial buffer
+    int work;     // work item (or first partial slot, see k_reduce)
     int row;      // row within the work item
     int col;      // pair within the work item
-    int pad;
+    int pad;      // number of partial slots to sum when the caller passes nsplit <= 0
 };
 
 // ---- launchers (bsp_fft.cu) ----
@@ -83,21 +93,35 @@ cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const in
                               uint32_t* hi, uint32_t* lo, int f16, unsigned* fmax2, unsigned* f0max,
                               cudaStream_t st);
 
+// Shot-noise combination in the reduction: v -= sum_t coef[t] * (sum of partial set t).
+struct ShotTerms {
+    int n;
+    const double* partial[3];
+    double coef[3];
+};
+
 // ---- launchers (bsp_contract.cu) ----
 template <typename R>
-cudaError_t launch_contract_cc(const R* fields, size_t fstride, const Work* works, int nwork,
-                               const int2* pair_fields, const int* row_fields, size_t npts,
-                               int nsplit, double* partial, cudaStream_t st);
+cudaError_t launch_contract_cc(const R* rows, const R* px, const R* py, int sym, size_t fstride,
+                               const Work* works, int nwork, const int2* pair_fields,
+                               const int* row_fields, size_t npts, int nsplit, double* partial,
+                               cudaStream_t st);
 
 cudaError_t launch_reduce(const double* partial, int nsplit, size_t unit, int row_stride,
                           const BinLoc* loc, int nout, int nbins, const double* counts, double scale,
-                          int mode, double* T_out, double* out, cudaStream_t st);
+                          int mode, double* T_out, double* out, cudaStream_t st,
+                          const ShotTerms* shot = nullptr);
 
 // ---- launchers (bsp_tc.cu) ----
 size_t tc_smem_bytes();
 cudaError_t launch_contract_tc(bool f16, const void* tm_f0, const void* tm_hi, const void* tm_lo,
-                               const TcWork* works, int nwork, const int2* pair_shells,
-                               const unsigned* f0max, const unsigned* fmax2, float bound_mul, size_t npts,
-                               int nsplit, int nprod, int chunk_kb, double* partial, int* err, cudaStream_t st);
+                               const TcWork* works, const TcUnit* units, int nunits, int lsup, int nsup,
+                               const int2* pair_shells, int pair_base, const unsigned* fmax2,
+                               float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
+                               cudaStream_t st);
+
+// ---- launchers (bsp_modal.cu) ----
+cudaError_t launch_modal_assemble(const double* T, const double* U, const int* ells, int n_ell, int nf,
+                                  long long nall, int ntrip, double scale, double* S, cudaStream_t st);
 
 }  // namespace bsp

@@ -170,12 +170,32 @@ __device__ __forceinline__ void unpack2(uint32_t v, float& x0, float& x1) {
     }
 }
 
-// Power of two s with bound * s in [2^14, 2^15) (see the FFT's pass 3).
-__device__ __forceinline__ float pow2_scale(float bound) {
+// Power of two s with bound * s in [2^(t-1), 2^t) (the FFT's pass 3 applies
+// the same scales: t = 15 to the 16-bit planes, t = 7 to the FP32 pair factors).
+__device__ __forceinline__ float pow2_scale(float bound, int t = 15) {
     if (!(bound > 0.f)) return 1.f;
     int e;
     frexpf(bound, &e);
-    return ldexpf(1.f, 15 - e);
+    return ldexpf(1.f, t - e);
+}
+
+__device__ __forceinline__ uint64_t fmul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fsub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t pack64(float x0, float x1) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(x0), "f"(x1));
+    return d;
+}
+__device__ __forceinline__ void unpack64(uint64_t v, float& x0, float& x1) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(v));
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -193,18 +213,22 @@ template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_contract_tc(const __grid_constant__ CUtensorMap tm_f0, const __grid_constant__ CUtensorMap tm_hi,
                   const __grid_constant__ CUtensorMap tm_lo, const TcWork* __restrict__ works,
-                  const int2* __restrict__ pair_shells, const unsigned* __restrict__ f0max,
-                  const unsigned* __restrict__ fmax2, float bound_mul, int nkb_total, int kb_per_split, int nprod,
-                  int CHUNK, double* __restrict__ partial, int* __restrict__ err) {
+                  const int2* __restrict__ pair_shells, int pair_base,
+                  const unsigned* __restrict__ fmax2, float bound_mul, const TcUnit* __restrict__ units,
+                  int lsup, int nsup, int nprod, int CHUNK, double* __restrict__ partial,
+                  int* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const TcUnit unit = units[blockIdx.x];
     if (tid < (int)(sizeof(TcWork) / sizeof(int)))
-        reinterpret_cast<int*>(&S.w)[tid] = reinterpret_cast<const int*>(works + blockIdx.x)[tid];
+        reinterpret_cast<int*>(&S.w)[tid] = reinterpret_cast<const int*>(works + unit.work)[tid];
     __syncthreads();
     const TcWork& w = S.w;
-    const int kb0 = blockIdx.y * kb_per_split;
-    const int nkb = max(0, min(nkb_total, kb0 + kb_per_split) - kb0);
+    // iteration k covers K-block (k / len) * lsup + start + k % len: every CTA
+    // walks the super-segments in the same order (shared fields stay in L2);
+    // K-blocks past the end of the grid load as zeros and add nothing
+    const int nkb = nsup * unit.len;
     const int nch = (nkb + CHUNK - 1) / CHUNK;
     const uint32_t N = (uint32_t)w.n;
 
@@ -229,8 +253,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float sc = 1.f;
         if (tid < w.npairs) {
             v = pair_shells[w.pair0 + tid];
-            // exact max |F_b| |F_c| bounds the pair product: scale it below 2^15
-            sc = pow2_scale(__uint_as_float(f0max[v.x]) * __uint_as_float(f0max[v.y]));
+            // the FP32 pair factors arrive pre-scaled by s7 each (|F s7| < 2^7): the
+            // pair product carries s7_b s7_c, undone at the end
+            sc = pow2_scale(bound_mul * __uint_as_float(fmax2[pair_base + v.x]), 7) *
+                 pow2_scale(bound_mul * __uint_as_float(fmax2[pair_base + v.y]), 7);
             v.x -= w.shell_lo;
             v.y -= w.shell_lo;
         }
@@ -268,7 +294,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 mbar_expect_tx(&S.tma_full[s], bytes);
-                const int x0 = (kb0 + k) * TC_KB;
+                const int x0 = ((k / unit.len) * lsup + unit.start + k % unit.len) * TC_KB;
                 for (int j = 0; j < nfb; ++j)
                     tma_load_2d(&S.f0[s][j * 8 * TC_KB], &tm_f0, x0, w.shell_lo + 8 * j, &S.tma_full[s]);
                 for (int j = 0; j < nbb; ++j) {
@@ -335,18 +361,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int r = 0; r < TC_M / N_PRO; ++r) {
                 const int i = wr * (TC_M / N_PRO) + r;
                 const int2 bc = S.pf[i];
-                float p0 = 0.f, p1 = 0.f;
+                uint64_t p = 0;
                 if (bc.x >= 0) {
-                    const float2 fb = *reinterpret_cast<const float2*>(&f0[bc.x * TC_KB + 2 * lane]);
-                    const float2 fc = *reinterpret_cast<const float2*>(&f0[bc.y * TC_KB + 2 * lane]);
-                    const float sc = S.pscale[i];
-                    p0 = fb.x * fc.x * sc;
-                    p1 = fb.y * fc.y * sc;
+                    const uint64_t fb = *reinterpret_cast<const uint64_t*>(&f0[bc.x * TC_KB + 2 * lane]);
+                    const uint64_t fc = *reinterpret_cast<const uint64_t*>(&f0[bc.y * TC_KB + 2 * lane]);
+                    p = fmul2(fb, fc);
                 }
+                float p0, p1, h0, h1;
+                unpack64(p, p0, p1);
                 const uint32_t hi = pack2<F16>(p0, p1);
-                float h0, h1;
                 unpack2<F16>(hi, h0, h1);
-                const uint32_t lo = pack2<F16>(p0 - h0, p1 - h1);
+                float r0, r1;
+                unpack64(fsub2(p, pack64(h0, h1)), r0, r1);
+                const uint32_t lo = pack2<F16>(r0, r1);
                 // element (i, k = 2 lane): 16-byte chunk lane/4, swizzled by row i mod 8
                 const int off = (i >> 3) * 1024 + (i & 7) * 128 + (((lane >> 2) ^ (i & 7)) << 4) + ((lane & 3) << 2);
                 *reinterpret_cast<uint32_t*>(ah + off) = hi;
@@ -396,8 +423,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         // final: hi + lo in FP64, unscaled, to this CTA's partial slot
         const int row = 32 * q + lane;
-        double* dst = partial + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (TC_M * TC_NMAX) +
-                      (size_t)row * TC_NMAX;
+        double* dst = partial + (size_t)blockIdx.x * (TC_M * TC_NMAX) + (size_t)row * TC_NMAX;
         const bool have = nch > 0 && !S.abort;
         if (have) tc_fence_after();
         for (uint32_t col = 0; col < N; col += 16) {
@@ -429,30 +455,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
 cudaError_t launch_contract_tc(bool f16, const void* tm_f0, const void* tm_hi, const void* tm_lo,
-                               const TcWork* works, int nwork, const int2* pair_shells, const unsigned* f0max,
-                               const unsigned* fmax2, float bound_mul, size_t npts, int nsplit, int nprod,
-                               int chunk_kb, double* partial, int* err, cudaStream_t st) {
-    const int nkb_total = (int)((npts + TC_KB - 1) / TC_KB);
-    const int kb_per_split = (nkb_total + nsplit - 1) / nsplit;
+                               const TcWork* works, const TcUnit* units, int nunits, int lsup, int nsup,
+                               const int2* pair_shells, int pair_base, const unsigned* fmax2,
+                               float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
+                               cudaStream_t st) {
     const size_t smem = tc_smem_bytes();
     const CUtensorMap& a = *reinterpret_cast<const CUtensorMap*>(tm_f0);
     const CUtensorMap& b = *reinterpret_cast<const CUtensorMap*>(tm_hi);
     const CUtensorMap& c = *reinterpret_cast<const CUtensorMap*>(tm_lo);
-    dim3 grid(nwork, nsplit);
+    static bool set16 = false, setb = false;   // once per kernel, never inside a graph capture
     cudaError_t e;
     if (f16) {
-        if ((e = cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem)) != cudaSuccess)
-            return e;
-        k_contract_tc<true><<<grid, TC_THREADS, smem, st>>>(a, b, c, works, pair_shells, f0max, fmax2, bound_mul,
-                                                            nkb_total, kb_per_split, nprod, chunk_kb, partial, err);
+        if (!set16) {
+            if ((e = cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess)
+                return e;
+            set16 = true;
+        }
+        k_contract_tc<true><<<nunits, TC_THREADS, smem, st>>>(a, b, c, works, pair_shells, pair_base, fmax2, bound_mul,
+                                                              units, lsup, nsup, nprod, chunk_kb, partial, err);
     } else {
-        if ((e = cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem)) != cudaSuccess)
-            return e;
-        k_contract_tc<false><<<grid, TC_THREADS, smem, st>>>(a, b, c, works, pair_shells, f0max, fmax2,
-                                                             bound_mul, nkb_total, kb_per_split, nprod, chunk_kb,
-                                                             partial, err);
+        if (!setb) {
+            if ((e = cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess)
+                return e;
+            setb = true;
+        }
+        k_contract_tc<false><<<nunits, TC_THREADS, smem, st>>>(a, b, c, works, pair_shells, pair_base, fmax2,
+                                                               bound_mul, units, lsup, nsup, nprod, chunk_kb,
+                                                               partial, err);
     }
     return cudaGetLastError();
 }
