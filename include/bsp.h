@@ -299,6 +299,33 @@ bsp_status bsp_phase_times(bsp_plan* plan, double* ms, int* ncalls, int* launche
 
 
 
+/*
+ * Triple sums without any device allocation.  The paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc (a CUDA graph under
+ * capture, a host runtime that owns all device memory in a fixed pool, a
+ * hard memory budget).
+ *
+ *   T[t] = sum_{x < npts} F_i(x) F_j(x) F_k(x),  (i, j, k) = triplets[3t..3t+2],
+ *
+ * over caller fields F_f = fields + f * npts (device, FP32, [nfields][npts],
+ * 16-byte aligned).  triplets is HOST int32 [ntrip][3] with every index in
+ * [0, nfields); T is device FP64 [ntrip] (8-byte aligned), written.  Sums
+ * use FP32 products folded 64 at a time into compensated FP32 pairs, then
+ * FP64 across segments (the same accuracy as the BSP_FP32 contraction).
+ *
+ * Scratch: a 131 072-triplet list (1.5 MiB) and 2 097 152 FP64 partial sums
+ * (16 MiB) live in fixed device arrays that every GPU loading the library
+ * holds until the process exits.  ntrip above 131 072 is rejected with
+ * BSP_EINVAL.  Every call reuses the same arrays; nothing in them needs to
+ * start at zero (each partial is written before it is read), but calls that
+ * overlap on the GPU (different streams, or host threads) race on them.
+ * The first call on each device looks up the arrays' device addresses;
+ * make that first call before any stream capture.  Asynchronous on
+ * `stream` except for the triplet upload from pageable host memory.
+ */
+bsp_status bsp_triple_sums_static(const float* fields, size_t npts, int nfields,
+                                  const int32_t* triplets, int ntrip, double* T, void* stream);
+
 /* Human-readable text for a status, and the last CUDA error text seen by
  * this thread ("" if none). */
 const char* bsp_status_string(int status);

@@ -64,6 +64,7 @@ _SIGS = [
     ("bsp_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
     ("bsp_phase_times", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int)]),
+    ("bsp_triple_sums_static", ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     ("bsp_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("bsp_last_error", ctypes.c_char_p, []),
     ("bsp_version", ctypes.c_int, []),
@@ -269,6 +270,14 @@ def bsp_phase_times(plan: int):
     nc, nl = ctypes.c_int(), ctypes.c_int()
     _check(load().bsp_phase_times(plan, ms, ctypes.byref(nc), ctypes.byref(nl)), "bsp_phase_times")
     return list(ms), nc.value, nl.value
+
+
+def bsp_triple_sums_static(fields, npts: int, nfields: int, triplets: np.ndarray, T, stream=None):
+    """T[t] = sum_x F_i F_j F_k with no device allocation (fields, T: CUDA
+    tensors or device pointers; triplets: host int32 [ntrip][3])."""
+    tr = np.ascontiguousarray(triplets, dtype=np.int32).reshape(-1, 3)
+    _check(load().bsp_triple_sums_static(_dptr(fields), int(npts), int(nfields), tr.ctypes.data, int(tr.shape[0]),
+                                         _dptr(T), _stream_handle(stream)), "bsp_triple_sums_static")
 
 
 def bsp_version() -> int:
