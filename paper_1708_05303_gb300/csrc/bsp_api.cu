@@ -313,9 +313,9 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D map over rows x npts elements, box = 64 elements x 8 rows.
+// 2-D map over rows x npts elements, box = box_x elements x box_rows rows.
 bsp_status encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, size_t esize, size_t rows, size_t npts,
-                      bool swizzle) {
+                      bool swizzle, unsigned box_x, unsigned box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) {
         g_last_error = "cuTensorMapEncodeTiled unavailable";
@@ -323,7 +323,7 @@ bsp_status encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, size_t
     }
     cuuint64_t dims[2] = {(cuuint64_t)npts, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(npts * esize)};
-    cuuint32_t box[2] = {64, 8};
+    cuuint32_t box[2] = {box_x, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -332,6 +332,24 @@ bsp_status encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, size_t
         g_last_error = "cuTensorMapEncodeTiled failed: " + std::to_string((int)r);
         return BSP_ECUDA;
     }
+    return BSP_OK;
+}
+
+// The tensor-core contraction's maps: F0 rows [f0_rows][npts] FP32 in boxes of
+// 32 points x 8 << i rows, and the 16-bit planes [plane_rows][npts] in boxes of
+// 64 points x 8 << i rows, all 128-byte swizzled (lo = hi for one product).
+bsp_status encode_tc_maps(TcMaps* m, float* f0, size_t f0_rows, void* hi, void* lo, size_t plane_rows, size_t npts,
+                          bool f16) {
+    const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    bsp_status s;
+    for (int i = 0; i < TC_F0_MAPS; ++i)
+        if ((s = encode_map(&m->f0[i], f0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f0_rows, npts, true, 32, 8u << i)) !=
+            BSP_OK)
+            return s;
+    for (int i = 0; i < TC_PLANE_MAPS; ++i)
+        if ((s = encode_map(&m->hi[i], hi, t16, 2, plane_rows, npts, true, 64, 8u << i)) != BSP_OK ||
+            (s = encode_map(&m->lo[i], lo ? lo : hi, t16, 2, plane_rows, npts, true, 64, 8u << i)) != BSP_OK)
+            return s;
     return BSP_OK;
 }
 
@@ -967,16 +985,14 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
             launches += 3;
         }
         if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
-        CUtensorMap tmf0, tmhi, tmlo;
+        TcMaps maps;
         bsp_status es;
-        const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-        if ((es = encode_map(&tmf0, f0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->nsh, p->npts(), false)) != BSP_OK ||
-            (es = encode_map(&tmhi, hi, t16, 2, nf, p->npts(), true)) != BSP_OK ||
-            (es = encode_map(&tmlo, p->nprod == 3 ? (void*)lo : (void*)hi, t16, 2, nf, p->npts(), true)) != BSP_OK)
+        if ((es = encode_tc_maps(&maps, f0, p->nsh, hi, p->nprod == 3 ? lo : nullptr, nf, p->npts(), f16 != 0)) !=
+            BSP_OK)
             return es;
         double* partial = (double*)(base + L.partial);
         double* tout = (double*)(base + L.tout);
-        cudaError_t e = launch_contract_tc(f16 != 0, &tmf0, &tmhi, &tmlo, p->d_tc_works, p->d_tc_units,
+        cudaError_t e = launch_contract_tc(f16 != 0, maps, p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
                                            p->chunk_kb, partial, p->d_err, st);
@@ -1116,28 +1132,24 @@ bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* s
             launches += 3;
         }
         if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
-        const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-        CUtensorMap tmf0, tmf2, tmhi, tmlo;
+        TcMaps maps, maps2;
         bsp_status es;
-        if ((es = encode_map(&tmf0, f0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nf, p->npts(), false)) != BSP_OK ||
-            (es = encode_map(&tmhi, hi, t16, 2, nfields, p->npts(), true)) != BSP_OK ||
-            (es = encode_map(&tmlo, p->nprod == 3 ? (void*)lo : (void*)hi, t16, 2, nfields, p->npts(), true)) !=
-                BSP_OK)
+        if ((es = encode_tc_maps(&maps, f0, nf, hi, p->nprod == 3 ? lo : nullptr, nfields, p->npts(), f16 != 0)) !=
+            BSP_OK)
             return es;
-        if (p->need_u &&
-            (es = encode_map(&tmf2, f0 + (size_t)nf * p->npts(), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nf, p->npts(),
-                             false)) != BSP_OK)
+        if (p->need_u && (es = encode_tc_maps(&maps2, f0 + (size_t)nf * p->npts(), nf, hi,
+                                              p->nprod == 3 ? lo : nullptr, nfields, p->npts(), f16 != 0)) != BSP_OK)
             return es;
         double* part = (double*)(base + L.partial);
         double* upart = (double*)(base + L.partial + p->tc_part_bytes);
-        cudaError_t e = launch_contract_tc(f16 != 0, &tmf0, &tmhi, &tmlo, p->d_tc_works, p->d_tc_units,
+        cudaError_t e = launch_contract_tc(f16 != 0, maps, p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
                                            p->chunk_kb, part, p->d_err, st);
         if (e != cudaSuccess) return cuda_fail(e, "contract (modal, tensor cores)");
         ++launches;
         if (p->need_u) {
-            e = launch_contract_tc(f16 != 0, &tmf2, &tmhi, &tmlo, p->d_tcu_works, p->d_tcu_units,
+            e = launch_contract_tc(f16 != 0, maps2, p->d_tcu_works, p->d_tcu_units,
                                    (int)p->tc_u_sched.units.size(), p->tc_u_sched.lsup, p->tc_u_sched.nsup,
                                    p->d_tcu_pairs, p->slot2 * nf, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
                                    p->chunk_kb, upart, p->d_err, st);

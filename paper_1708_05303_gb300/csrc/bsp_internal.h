@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/bsp.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -113,10 +114,20 @@ cudaError_t launch_reduce(const double* partial, int nsplit, size_t unit, int ro
                           const ShotTerms* shot = nullptr);
 
 // ---- launchers (bsp_tc.cu) ----
+// Tensor maps of one tensor-core contraction, one per box height: F0 rows
+// (FP32, boxes of 32 points x 8 << i rows, 128-byte swizzle) and the 16-bit
+// hi / lo planes (boxes of 64 points x 8 << i rows, 128-byte swizzle).
+constexpr int TC_F0_MAPS = 4;      // 8, 16, 32, 64 rows
+constexpr int TC_PLANE_MAPS = 5;   // 8, 16, 32, 64, 128 rows
+struct TcMaps {
+    CUtensorMap f0[TC_F0_MAPS];
+    CUtensorMap hi[TC_PLANE_MAPS];
+    CUtensorMap lo[TC_PLANE_MAPS];
+};
+
 size_t tc_smem_bytes();
-cudaError_t launch_contract_tc(bool f16, const void* tm_f0, const void* tm_hi, const void* tm_lo,
-                               const TcWork* works, const TcUnit* units, int nunits, int lsup, int nsup,
-                               const int2* pair_shells, int pair_base, const unsigned* fmax2,
+cudaError_t launch_contract_tc(bool f16, const TcMaps& maps, const TcWork* works, const TcUnit* units, int nunits,
+                               int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
                                cudaStream_t st);
 

@@ -7,23 +7,25 @@
 // A CTA owns one tile -- 128 pairs (the MMA M) times N <= 128 field rows --
 // and one x-segment, and runs a warp-specialised pipeline per K-block of 64
 // points:
-//   warp 0      TMA: F^0 rows (FP32) for the pairs, and the 16-bit hi/lo
-//               planes of the tile's field rows (128-byte swizzled boxes);
-//   warps 4-11  form P = F_b F_c in FP32, split it into 16-bit hi + lo,
-//               and store both in the K-major 128-byte-swizzled layout the
-//               MMA reads;
-//   warp 1      one thread issues tcgen05.mma kind::f16, M=128, K=16:
+//   warp 0      TMA: F^0 rows (FP32) of the tile's shells and the 16-bit
+//               hi/lo planes of its field rows, a few large 128-byte-swizzled
+//               boxes per K-block, four stages deep;
+//   warps 4-11  form P = F_b F_c in FP32 (one pair per TMEM lane, half a
+//               K-block per warp), split it into 16-bit hi + lo and store
+//               both in tensor memory, where the MMA reads its A operand;
+//   warp 1      one thread issues tcgen05.mma kind::f16, M=128, K=16, A from
+//               tensor memory, B (field planes) from shared memory:
 //               D += P_hi F_hi + P_hi F_lo + P_lo F_hi (split products;
 //               one product for the plain 16-bit mode), FP32 accumulators
 //               in tensor memory;
-//   warps 12-15 drain the accumulator every `chunk` K-blocks (tcgen05.ld) and
-//               fold it into compensated FP32 (TwoSum hi + lo) running sums
-//               kept in tensor memory, written once to FP64 at the end.
-// A three-stage TMA ring, two pair-product buffers and two accumulator
-// buffers keep TMA, the CUDA-core prologue, the MMAs and the epilogue
-// overlapped.  Every mbarrier wait is
-// bounded; on timeout the CTA records an error code, stops, waits (bounded)
-// for its own copies in flight and releases its tensor memory.
+//   warps 12-15 drain the accumulator every `chunk` K-blocks (tcgen05.ld),
+//               add it to a running FP32 sum in tensor memory, and every
+//               FLUSH_KB K-blocks add that sum, unscaled, to the CTA's FP64
+//               slot in global memory.
+// Two accumulator buffers and two A buffers in tensor memory keep TMA, the
+// CUDA-core prologue, the MMAs and the epilogue overlapped.  Every mbarrier
+// wait is bounded; on timeout the CTA records an error code, stops, waits
+// (bounded) for its own copies in flight and releases its tensor memory.
 #include <cuda.h>
 
 #include "bsp_internal.h"
@@ -35,23 +37,25 @@ namespace {
 constexpr int TC_M = 128;        // pairs per tile = MMA M
 constexpr int TC_NMAX = 128;     // field rows per tile = MMA N (max)
 constexpr int TC_KB = 64;        // x-points per K-block (128 bytes of 16-bit values)
-constexpr int NT = 3;            // TMA ring stages (F0 rows + field planes)
-constexpr int NA = 2;            // pair-product (A operand) buffers
+constexpr int NT = 4;            // TMA ring stages (F0 rows + field planes)
 constexpr int TC_MAXSH = 64;     // F0 rows per tile
 constexpr int TC_THREADS = 512;  // 16 warps
 constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, N_PRO = 8, W_EPI0 = 12;
-constexpr uint32_t TMEM_COLS = 512;   // acc0 [0,128) acc1 [128,256) hi [256,384) lo [384,512)
+// tensor memory columns: acc0 [0,128) acc1 [128,256) running sum [256,384)
+// A buffers [384,448) and [448,512): hi in the first 32 columns, lo in the next 32
+constexpr uint32_t TMEM_COLS = 512, COL_SUM = 256, COL_A = 384;
+constexpr int FLUSH_KB = 128;    // K-blocks between FP64 flushes of the running sum
 constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
 
 struct TcSmem {
-    uint8_t a_hi[NA][TC_M * 128];
-    uint8_t a_lo[NA][TC_M * 128];
+    float f0[NT][2][TC_MAXSH * 32];     // [stage][half of the K-block][row][32 points], swizzled
     uint8_t b_hi[NT][TC_NMAX * 128];
     uint8_t b_lo[NT][TC_NMAX * 128];
-    float f0[NT][TC_MAXSH * TC_KB];
-    uint64_t tma_full[NT], tma_empty[NT], a_full[NA], a_empty[NA], acc_full[2], acc_empty[2];
+    uint64_t tma_full[NT], tma_empty[NT], a_full[2], a_empty[2], acc_full[2], acc_empty[2];
     uint32_t tmem_base;
     volatile int abort;
+    int npc;                  // plane copies per K-block
+    int4 pc[16];              // plane copy: (map, first field row, first box, -)
     int2 pf[TC_M];
     float pscale[TC_M];
     float fscale[TC_NMAX];
@@ -100,11 +104,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void mma_16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// D (tensor memory) += A (tensor memory, M x 16, one row per lane) * B (shared memory)^T
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -198,12 +203,6 @@ __device__ __forceinline__ void unpack64(uint64_t v, float& x0, float& x1) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(v));
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
 __device__ __forceinline__ void set_abort(TcSmem& S, int* err, int code) {
     S.abort = 1;
     atomicOr(err, code);
@@ -211,8 +210,7 @@ __device__ __forceinline__ void set_abort(TcSmem& S, int* err, int code) {
 
 template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_contract_tc(const __grid_constant__ CUtensorMap tm_f0, const __grid_constant__ CUtensorMap tm_hi,
-                  const __grid_constant__ CUtensorMap tm_lo, const TcWork* __restrict__ works,
+    k_contract_tc(const __grid_constant__ TcMaps maps, const TcWork* __restrict__ works,
                   const int2* __restrict__ pair_shells, int pair_base,
                   const unsigned* __restrict__ fmax2, float bound_mul, const TcUnit* __restrict__ units,
                   int lsup, int nsup, int nprod, int CHUNK, double* __restrict__ partial,
@@ -230,6 +228,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // K-blocks past the end of the grid load as zeros and add nothing
     const int nkb = nsup * unit.len;
     const int nch = (nkb + CHUNK - 1) / CHUNK;
+    const int FL = max(1, FLUSH_KB / CHUNK);   // chunks per FP64 flush
     const uint32_t N = (uint32_t)w.n;
 
     if (tid == 0) {
@@ -237,17 +236,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&S.tma_full[s], 1);
             mbar_init(&S.tma_empty[s], 1);
         }
-        for (int s = 0; s < NA; ++s) {
-            mbar_init(&S.a_full[s], N_PRO);
-            mbar_init(&S.a_empty[s], 1);
-        }
         for (int j = 0; j < 2; ++j) {
+            mbar_init(&S.a_full[j], N_PRO);
+            mbar_init(&S.a_empty[j], 1);
             mbar_init(&S.acc_full[j], 1);
             mbar_init(&S.acc_empty[j], 4);
         }
         S.abort = 0;
+        // field-plane copies: runs of consecutive 8-row boxes, split into
+        // boxes of 128, 64, 32, 16, 8 rows
+        int npc = 0;
+        for (int j = 0; j < w.nbox;) {
+            int L = 1;
+            while (j + L < w.nbox && w.box_field[j + L] == w.box_field[j] + 8 * L) ++L;
+            for (int m = TC_PLANE_MAPS - 1, off = 0; m >= 0; --m)
+                while (L - off >= (1 << m)) {
+                    S.pc[npc++] = make_int4(m, w.box_field[j + off], j + off, 0);
+                    off += 1 << m;
+                }
+            j += L;
+        }
+        S.npc = npc;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // MMA rows past the tile's boxes (N rounds 8 nbox up to 16) read zeros
+    for (int i = tid; i < NT * 2 * ((int)N - 8 * w.nbox) * 32; i += TC_THREADS) {
+        const int per = ((int)N - 8 * w.nbox) * 32, s = i / per, r = i % per;
+        uint8_t* base = (s & 1) ? S.b_lo[s >> 1] : S.b_hi[s >> 1];
+        reinterpret_cast<uint32_t*>(base + 8 * w.nbox * 128)[r] = 0u;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid < TC_M) {
         int2 v = {-1, -1};
         float sc = 1.f;
@@ -283,9 +301,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (warp == W_TMA) {
         if (lane == 0) {
-            const int nfb = (w.nshell + 7) >> 3;
-            const int nbb = (int)N >> 3;   // boxes including the padding box
-            const uint32_t bytes = (uint32_t)nfb * 8 * TC_KB * 4 + (uint32_t)nbb * 1024 * 2;
+            const int nfb = (w.nshell + 7) >> 3;   // 8-row F0 boxes per half K-block
+            const int npc = S.npc;
+            const bool two = nprod == 3;
+            const uint32_t bytes = (uint32_t)nfb * 2048 + (uint32_t)w.nbox * 1024 * (two ? 2 : 1);
             int issued = 0;
             for (int k = 0; k < nkb && !S.abort; ++k) {
                 const int s = k % NT, u = k / NT;
@@ -295,12 +314,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 mbar_expect_tx(&S.tma_full[s], bytes);
                 const int x0 = ((k / unit.len) * lsup + unit.start + k % unit.len) * TC_KB;
-                for (int j = 0; j < nfb; ++j)
-                    tma_load_2d(&S.f0[s][j * 8 * TC_KB], &tm_f0, x0, w.shell_lo + 8 * j, &S.tma_full[s]);
-                for (int j = 0; j < nbb; ++j) {
-                    const int f = w.box_field[j < w.nbox ? j : w.nbox - 1];
-                    tma_load_2d(&S.b_hi[s][j * 1024], &tm_hi, x0, f, &S.tma_full[s]);
-                    tma_load_2d(&S.b_lo[s][j * 1024], &tm_lo, x0, f, &S.tma_full[s]);
+                for (int h = 0; h < 2; ++h)
+                    for (int m = TC_F0_MAPS - 1, off = 0; m >= 0; --m)
+                        if (nfb - off >= (1 << m)) {
+                            tma_load_2d(&S.f0[s][h][off * 8 * 32], &maps.f0[m], x0 + 32 * h, w.shell_lo + 8 * off,
+                                        &S.tma_full[s]);
+                            off += 1 << m;
+                        }
+                for (int j = 0; j < npc; ++j) {
+                    const int4 c = S.pc[j];
+                    tma_load_2d(&S.b_hi[s][c.z * 1024], &maps.hi[c.x], x0, c.y, &S.tma_full[s]);
+                    if (two) tma_load_2d(&S.b_lo[s][c.z * 1024], &maps.lo[c.x], x0, c.y, &S.tma_full[s]);
                 }
                 issued = k + 1;
             }
@@ -313,7 +337,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t idesc = make_idesc(F16 ? 0u : 1u, N);
             int done = 0;
             for (int k = 0; k < nkb && !S.abort; ++k) {
-                const int s = k % NT, u = k / NT, sa = k % NA, ua = k / NA;
+                const int s = k % NT, u = k / NT, sa = k & 1, ua = k >> 1;
                 const int c = k / CHUNK, j = c & 1;
                 const bool first = (k % CHUNK) == 0;
                 const bool last = (k % CHUNK) == CHUNK - 1 || k == nkb - 1;
@@ -327,15 +351,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(j * 128);
-                const uint32_t ah = smem_u32(S.a_hi[sa]), al = smem_u32(S.a_lo[sa]);
+                const uint32_t ah = tmem + COL_A + (uint32_t)sa * 64, al = ah + 32;
                 const uint32_t bh = smem_u32(S.b_hi[s]), bl = smem_u32(S.b_lo[s]);
 #pragma unroll
                 for (int kk = 0; kk < TC_KB / 16; ++kk) {
-                    const uint32_t o = (uint32_t)kk * 32;
-                    mma_16(d, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (first && kk == 0) ? 0u : 1u);
+                    const uint32_t o = (uint32_t)kk * 32, oa = (uint32_t)kk * 8;
+                    mma_ts(d, ah + oa, sw128_desc(bh + o), idesc, (first && kk == 0) ? 0u : 1u);
                     if (nprod == 3) {
-                        mma_16(d, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1u);
-                        mma_16(d, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1u);
+                        mma_ts(d, ah + oa, sw128_desc(bl + o), idesc, 1u);
+                        mma_ts(d, al + oa, sw128_desc(bh + o), idesc, 1u);
                     }
                 }
                 mma_commit(&S.tma_empty[s]);
@@ -344,102 +368,97 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 done = k + 1;
             }
             // the last MMAs must finish before tensor memory is released
-            if (done > 0 && !mbar_wait(&S.a_empty[(done - 1) % NA], ((done - 1) / NA) & 1)) atomicOr(err, 32);
+            if (done > 0 && !mbar_wait(&S.a_empty[(done - 1) & 1], ((done - 1) >> 1) & 1)) atomicOr(err, 32);
         }
     } else if (warp >= W_PRO0 && warp < W_PRO0 + N_PRO) {
-        const int wr = warp - W_PRO0;
+        // lane quadrant q of tensor memory = pairs 32 q .. 32 q + 31; half h of each K-block
+        const int q = warp & 3, h = (warp - W_PRO0) >> 2;
+        const int i = 32 * q + lane;
+        const int2 bc = S.pf[i];
+        const bool live = bc.x >= 0;
+        const int rb = live ? bc.x : 0, rc = live ? bc.y : 0;
+        // row r, 16-byte chunk j of a 128-byte-swizzled F0 half lives at r*128 + ((j ^ (r & 7)) << 4)
+        const int ob = rb * 128, sb = rb & 7, oc = rc * 128, sc = rc & 7;
+        const uint32_t lanebase = ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h);
         for (int k = 0; k < nkb && !S.abort; ++k) {
-            const int s = k % NT, u = k / NT, sa = k % NA, ua = k / NA;
+            const int s = k % NT, u = k / NT, sa = k & 1, ua = k >> 1;
             if (!mbar_wait(&S.tma_full[s], u & 1) || (ua > 0 && !mbar_wait(&S.a_empty[sa], (ua - 1) & 1))) {
                 set_abort(S, err, 8);
                 break;
             }
-            const float* f0 = S.f0[s];
-            uint8_t* ah = S.a_hi[sa];
-            uint8_t* al = S.a_lo[sa];
-#pragma unroll 4
-            for (int r = 0; r < TC_M / N_PRO; ++r) {
-                const int i = wr * (TC_M / N_PRO) + r;
-                const int2 bc = S.pf[i];
-                uint64_t p = 0;
-                if (bc.x >= 0) {
-                    const uint64_t fb = *reinterpret_cast<const uint64_t*>(&f0[bc.x * TC_KB + 2 * lane]);
-                    const uint64_t fc = *reinterpret_cast<const uint64_t*>(&f0[bc.y * TC_KB + 2 * lane]);
-                    p = fmul2(fb, fc);
+            tc_fence_after();
+            const uint8_t* f0 = reinterpret_cast<const uint8_t*>(S.f0[s][h]);
+            uint32_t vh[16], vl[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                uint64_t p01 = 0, p23 = 0;
+                if (live) {
+                    const float4 fb = *reinterpret_cast<const float4*>(f0 + ob + ((j ^ sb) << 4));
+                    const float4 fc = *reinterpret_cast<const float4*>(f0 + oc + ((j ^ sc) << 4));
+                    p01 = fmul2(pack64(fb.x, fb.y), pack64(fc.x, fc.y));
+                    p23 = fmul2(pack64(fb.z, fb.w), pack64(fc.z, fc.w));
                 }
-                float p0, p1, h0, h1;
-                unpack64(p, p0, p1);
-                const uint32_t hi = pack2<F16>(p0, p1);
-                unpack2<F16>(hi, h0, h1);
-                float r0, r1;
-                unpack64(fsub2(p, pack64(h0, h1)), r0, r1);
-                const uint32_t lo = pack2<F16>(r0, r1);
-                // element (i, k = 2 lane): 16-byte chunk lane/4, swizzled by row i mod 8
-                const int off = (i >> 3) * 1024 + (i & 7) * 128 + (((lane >> 2) ^ (i & 7)) << 4) + ((lane & 3) << 2);
-                *reinterpret_cast<uint32_t*>(ah + off) = hi;
-                *reinterpret_cast<uint32_t*>(al + off) = lo;
+                float p0, p1, p2, p3, h0, h1, h2, h3;
+                unpack64(p01, p0, p1);
+                unpack64(p23, p2, p3);
+                vh[2 * j] = pack2<F16>(p0, p1);
+                vh[2 * j + 1] = pack2<F16>(p2, p3);
+                unpack2<F16>(vh[2 * j], h0, h1);
+                unpack2<F16>(vh[2 * j + 1], h2, h3);
+                float r0, r1, r2, r3;
+                unpack64(fsub2(p01, pack64(h0, h1)), r0, r1);
+                unpack64(fsub2(p23, pack64(h2, h3)), r2, r3);
+                vl[2 * j] = pack2<F16>(r0, r1);
+                vl[2 * j + 1] = pack2<F16>(r2, r3);
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const uint32_t ta = tmem + lanebase + COL_A + (uint32_t)sa * 64;
+            tmem_st16(ta, vh);
+            if (nprod == 3) tmem_st16(ta + 32, vl);
+            tmem_st_wait();
+            tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.a_full[sa]);
         }
     } else if (warp >= W_EPI0) {
         const int q = warp & 3;
         const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
+        const int row = 32 * q + lane;
+        double* dst = partial + (size_t)blockIdx.x * (TC_M * TC_NMAX) + (size_t)row * TC_NMAX;
+        const double rs = 1.0 / (double)S.pscale[row];   // exact: powers of two
         for (int c = 0; c < nch && !S.abort; ++c) {
-            const int j = c & 1;
+            const int j = c & 1, g = c % FL;
+            const bool flush = g == FL - 1 || c == nch - 1, first_flush = c < FL;
             if (!mbar_wait(&S.acc_full[j], (c >> 1) & 1)) {
                 set_abort(S, err, 64);
                 break;
             }
             tc_fence_after();
             for (uint32_t col = 0; col < N; col += 16) {
-                uint32_t a[16], h[16], l[16];
+                uint32_t a[16], m[16];
                 tmem_ld16(lanebase + (uint32_t)(j * 128) + col, a);
-                if (c > 0) {
-                    tmem_ld16(lanebase + 256 + col, h);
-                    tmem_ld16(lanebase + 384 + col, l);
-                }
+                if (g > 0) tmem_ld16(lanebase + COL_SUM + col, m);
                 tmem_ld_wait();
+                if (g > 0) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    if (c == 0) {
-                        h[i] = a[i];
-                        l[i] = 0u;
-                    } else {
-                        float s, e;
-                        two_sum(__uint_as_float(h[i]), __uint_as_float(a[i]), s, e);
-                        h[i] = __float_as_uint(s);
-                        l[i] = __float_as_uint(__uint_as_float(l[i]) + e);
-                    }
+                    for (int t = 0; t < 16; ++t) a[t] = __float_as_uint(__uint_as_float(m[t]) + __uint_as_float(a[t]));
                 }
-                tmem_st16(lanebase + 256 + col, h);
-                tmem_st16(lanebase + 384 + col, l);
+                if (flush) {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        const double v = (double)__uint_as_float(a[t]) * rs / (double)S.fscale[col + t];
+                        dst[col + t] = first_flush ? v : dst[col + t] + v;
+                    }
+                } else {
+                    tmem_st16(lanebase + COL_SUM + col, a);
+                }
             }
-            tmem_st_wait();
+            if (!flush) tmem_st_wait();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.acc_empty[j]);
         }
-        // final: hi + lo in FP64, unscaled, to this CTA's partial slot
-        const int row = 32 * q + lane;
-        double* dst = partial + (size_t)blockIdx.x * (TC_M * TC_NMAX) + (size_t)row * TC_NMAX;
-        const bool have = nch > 0 && !S.abort;
-        if (have) tc_fence_after();
-        for (uint32_t col = 0; col < N; col += 16) {
-            uint32_t h[16], l[16];
-            if (have) {
-                tmem_ld16(lanebase + 256 + col, h);
-                tmem_ld16(lanebase + 384 + col, l);
-                tmem_ld_wait();
-            }
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                double v = have ? (double)__uint_as_float(h[i]) + (double)__uint_as_float(l[i]) : 0.0;
-                v /= (double)S.pscale[row] * (double)S.fscale[col + i];
-                dst[col + i] = v;
-            }
-        }
+        if (nch == 0)
+            for (uint32_t col = 0; col < N; ++col) dst[col] = 0.0;
     }
     tc_fence_before();
     __syncthreads();
@@ -454,15 +473,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
-cudaError_t launch_contract_tc(bool f16, const void* tm_f0, const void* tm_hi, const void* tm_lo,
-                               const TcWork* works, const TcUnit* units, int nunits, int lsup, int nsup,
-                               const int2* pair_shells, int pair_base, const unsigned* fmax2,
+cudaError_t launch_contract_tc(bool f16, const TcMaps& maps, const TcWork* works, const TcUnit* units, int nunits,
+                               int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
                                cudaStream_t st) {
     const size_t smem = tc_smem_bytes();
-    const CUtensorMap& a = *reinterpret_cast<const CUtensorMap*>(tm_f0);
-    const CUtensorMap& b = *reinterpret_cast<const CUtensorMap*>(tm_hi);
-    const CUtensorMap& c = *reinterpret_cast<const CUtensorMap*>(tm_lo);
     static bool set16 = false, setb = false;   // once per kernel, never inside a graph capture
     cudaError_t e;
     if (f16) {
@@ -472,7 +487,7 @@ cudaError_t launch_contract_tc(bool f16, const void* tm_f0, const void* tm_hi, c
                 return e;
             set16 = true;
         }
-        k_contract_tc<true><<<nunits, TC_THREADS, smem, st>>>(a, b, c, works, pair_shells, pair_base, fmax2, bound_mul,
+        k_contract_tc<true><<<nunits, TC_THREADS, smem, st>>>(maps, works, pair_shells, pair_base, fmax2, bound_mul,
                                                               units, lsup, nsup, nprod, chunk_kb, partial, err);
     } else {
         if (!setb) {
@@ -481,7 +496,7 @@ cudaError_t launch_contract_tc(bool f16, const void* tm_f0, const void* tm_hi, c
                 return e;
             setb = true;
         }
-        k_contract_tc<false><<<nunits, TC_THREADS, smem, st>>>(a, b, c, works, pair_shells, pair_base, fmax2,
+        k_contract_tc<false><<<nunits, TC_THREADS, smem, st>>>(maps, works, pair_shells, pair_base, fmax2,
                                                                bound_mul, units, lsup, nsup, nprod, chunk_kb,
                                                                partial, err);
     }
