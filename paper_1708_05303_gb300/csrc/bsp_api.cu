@@ -335,20 +335,21 @@ bsp_status encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, size_t
     return BSP_OK;
 }
 
-// The tensor-core contraction's maps: F0 rows [f0_rows][npts] FP32 in boxes of
-// 32 points x 8 << i rows, and the 16-bit planes [plane_rows][npts] in boxes of
-// 64 points x 8 << i rows, all 128-byte swizzled (lo = hi for one product).
-bsp_status encode_tc_maps(TcMaps* m, float* f0, size_t f0_rows, void* hi, void* lo, size_t plane_rows, size_t npts,
+// The tensor-core contraction's maps over the K-block-major operands: F0
+// rows [nkb * f0_rows][64] FP32 in boxes of 32 points x 8 << i rows, and the
+// 16-bit planes [nkb * plane_rows][64] in boxes of 64 points x 8 << i rows,
+// all 128-byte swizzled (lo = hi for one product).
+bsp_status encode_tc_maps(TcMaps* m, float* f0, size_t f0_rows, void* hi, void* lo, size_t plane_rows, size_t nkb,
                           bool f16) {
     const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     bsp_status s;
     for (int i = 0; i < TC_F0_MAPS; ++i)
-        if ((s = encode_map(&m->f0[i], f0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f0_rows, npts, true, 32, 8u << i)) !=
-            BSP_OK)
+        if ((s = encode_map(&m->f0[i], f0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nkb * f0_rows, 64, true, 32,
+                            8u << i)) != BSP_OK)
             return s;
     for (int i = 0; i < TC_PLANE_MAPS; ++i)
-        if ((s = encode_map(&m->hi[i], hi, t16, 2, plane_rows, npts, true, 64, 8u << i)) != BSP_OK ||
-            (s = encode_map(&m->lo[i], lo ? lo : hi, t16, 2, plane_rows, npts, true, 64, 8u << i)) != BSP_OK)
+        if ((s = encode_map(&m->hi[i], hi, t16, 2, nkb * plane_rows, 64, true, 64, 8u << i)) != BSP_OK ||
+            (s = encode_map(&m->lo[i], lo ? lo : hi, t16, 2, nkb * plane_rows, 64, true, 64, 8u << i)) != BSP_OK)
             return s;
     return BSP_OK;
 }
@@ -435,6 +436,8 @@ struct bsp_plan {
         cand_dev.release(); comp_dev.release();
     }
     size_t npts() const { return (size_t)n * n * n; }
+    size_t nkb() const { return (npts() + 63) / 64; }   // K-blocks of 64 points
+    int kb_rows32 = 0, kb_rows16 = 0;   // rows per K-block of the tensor-core operands
     int nslot() const { return (int)slot_ell.size(); }
 };
 
@@ -623,7 +626,7 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     if ((st = upload(&p->d_shell_of, shell_of)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||
         (st = upload(&p->d_tw64, tw64)) != BSP_OK || (st = upload(&p->d_fd_delta, fdd)) != BSP_OK ||
         (st = upload(&p->d_fd_unit, fdu)) != BSP_OK || (st = upload(&p->d_fd_tc, fdt)) != BSP_OK ||
-        (st = upload(&p->d_err, std::vector<int>{0})) != BSP_OK ||
+        (st = upload(&p->d_err, std::vector<int>{0, 0, 0})) != BSP_OK ||
         (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)(p->nslot() + 1) * n_shells, 0u))) != BSP_OK) {
         delete p;
         return st;
@@ -661,8 +664,14 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     if (p->shot) p->part_bytes *= 4;   // main sum + three shot-noise sums
     p->tout_bytes = round256(p->ells.size() * p->cand.size() * sizeof(double));
     if (p->tc) {
-        p->f0_bytes = round256((size_t)n_shells * p->npts() * sizeof(float));
-        p->plane_bytes = round256(nfields32 * p->npts() * 2);
+        p->kb_rows32 = n_shells;
+        p->kb_rows16 = (int)nfields32;
+        if ((double)p->nkb() * (double)(p->kb_rows16 + n_shells) >= 2147483647.0) {   // TMA coordinates are 32-bit
+            delete p;
+            return BSP_EUNSUPPORTED;
+        }
+        p->f0_bytes = round256((size_t)n_shells * p->nkb() * 64 * sizeof(float));
+        p->plane_bytes = round256(nfields32 * p->nkb() * 64 * 2);
         TcSched tb = build_tc_sched(p->cand, p->out_slots, n_shells, p->npts(), p->nsm);
         p->tc_part_bytes = round256(std::max<size_t>((size_t)p->nsm, tb.units.size()) * TC_UNIT * sizeof(double));
     }
@@ -766,7 +775,7 @@ bsp_status bsp_plan_create_modal(bsp_plan** out, int n, double box, int n_funcs,
     bsp_status st;
     if ((st = upload(&p->d_radial, tab)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||
         (st = upload(&p->d_tw64, tw64)) != BSP_OK || (st = upload(&p->d_fd_delta, fdd)) != BSP_OK ||
-        (st = upload(&p->d_fd_tc, fdt)) != BSP_OK || (st = upload(&p->d_err, std::vector<int>{0})) != BSP_OK ||
+        (st = upload(&p->d_fd_tc, fdt)) != BSP_OK || (st = upload(&p->d_err, std::vector<int>{0, 0, 0})) != BSP_OK ||
         (st = upload(&p->d_ells, p->ells)) != BSP_OK ||
         (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)(p->nslot() + 2) * nf, 0u))) != BSP_OK) {
         delete p;
@@ -802,8 +811,14 @@ bsp_status bsp_plan_create_modal(bsp_plan** out, int n, double box, int n_funcs,
         }
     } else {
         p->tc_sched = build_tc_sched(p->bins, p->out_slots, nf, p->npts(), p->nsm);
-        p->f0_bytes = round256((p->need_u ? 2 : 1) * (size_t)nf * p->npts() * sizeof(float));
-        p->plane_bytes = round256(nfields * p->npts() * 2);
+        p->kb_rows32 = (p->need_u ? 2 : 1) * nf;
+        p->kb_rows16 = (int)nfields;
+        if ((double)p->nkb() * (double)(p->kb_rows16 + p->kb_rows32) >= 2147483647.0) {
+            delete p;
+            return BSP_EUNSUPPORTED;
+        }
+        p->f0_bytes = round256((size_t)p->kb_rows32 * p->nkb() * 64 * sizeof(float));
+        p->plane_bytes = round256(nfields * p->nkb() * 64 * 2);
         p->tc_part_bytes = round256(p->tc_sched.units.size() * TC_UNIT * sizeof(double));
         if ((st = upload(&p->d_tc_units, p->tc_sched.units)) != BSP_OK ||
             (st = upload(&p->d_tc_works, p->tc_sched.works)) != BSP_OK ||
@@ -974,28 +989,29 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
         const int nf = p->nslot() * p->nsh;
         unsigned* fmax2 = p->d_fmax;              // [nf]  max |T2| per field (bounds |F|)
         CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * (nf + p->nsh), st));
-        CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(p->d_err, 0, 3 * sizeof(int), st));   // error code, pacing counters
         const int f16 = p->prec == BSP_SPLIT_F16 ? 1 : 0;
         for (int f0i = 0; f0i < nf; f0i += p->fb32) {
             int nb = std::min(p->fb32, nf - f0i);
             cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, p->d_shell_of, nullptr,
                                                      p->d_fd_tc + f0i, nb, p->d_tw32, t1, t2, f0, p->npts(), hi,
-                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, nullptr, st);
+                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, nullptr, st,
+                                                     FieldLayout{p->kb_rows32, p->kb_rows16});
             if (e != cudaSuccess) return cuda_fail(e, "fft");
             launches += 3;
         }
         if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
         TcMaps maps;
         bsp_status es;
-        if ((es = encode_tc_maps(&maps, f0, p->nsh, hi, p->nprod == 3 ? lo : nullptr, nf, p->npts(), f16 != 0)) !=
-            BSP_OK)
+        if ((es = encode_tc_maps(&maps, f0, p->kb_rows32, hi, p->nprod == 3 ? lo : nullptr, p->kb_rows16, p->nkb(),
+                                 f16 != 0)) != BSP_OK)
             return es;
         double* partial = (double*)(base + L.partial);
         double* tout = (double*)(base + L.tout);
-        cudaError_t e = launch_contract_tc(f16 != 0, maps, p->d_tc_works, p->d_tc_units,
+        cudaError_t e = launch_contract_tc(f16 != 0, maps, p->kb_rows32, 0, p->kb_rows16, p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
-                                           p->chunk_kb, partial, p->d_err, st);
+                                           p->chunk_kb, partial, p->d_err, (unsigned*)p->d_err + 1, st);
         if (e != cudaSuccess) return cuda_fail(e, "contract (tensor cores)");
         if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
         const double V = p->box * p->box * p->box;
@@ -1121,38 +1137,36 @@ bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* s
         cx<float>* t2 = (cx<float>*)(base + L.t2);
         unsigned* fmax2 = p->d_fmax;                    // [nfields] max |T2| per field (bounds |F|)
         CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * (nfields + 2 * nf), st));
-        CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(p->d_err, 0, 3 * sizeof(int), st));   // error code, pacing counters
         const int f16 = p->prec == BSP_SPLIT_F16 ? 1 : 0;
         for (int fi = 0; fi < nfields; fi += p->fb32) {
             const int nb = std::min(p->fb32, nfields - fi);
             cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, nullptr, p->d_radial,
                                                      p->d_fd_tc + fi, nb, p->d_tw32, t1, t2, f0, p->npts(), hi,
-                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, nullptr, st);
+                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, nullptr, st,
+                                                     FieldLayout{p->kb_rows32, p->kb_rows16});
             if (e != cudaSuccess) return cuda_fail(e, "fft (modal)");
             launches += 3;
         }
         if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
-        TcMaps maps, maps2;
+        TcMaps maps;
         bsp_status es;
-        if ((es = encode_tc_maps(&maps, f0, nf, hi, p->nprod == 3 ? lo : nullptr, nfields, p->npts(), f16 != 0)) !=
-            BSP_OK)
-            return es;
-        if (p->need_u && (es = encode_tc_maps(&maps2, f0 + (size_t)nf * p->npts(), nf, hi,
-                                              p->nprod == 3 ? lo : nullptr, nfields, p->npts(), f16 != 0)) != BSP_OK)
+        if ((es = encode_tc_maps(&maps, f0, p->kb_rows32, hi, p->nprod == 3 ? lo : nullptr, p->kb_rows16, p->nkb(),
+                                 f16 != 0)) != BSP_OK)
             return es;
         double* part = (double*)(base + L.partial);
         double* upart = (double*)(base + L.partial + p->tc_part_bytes);
-        cudaError_t e = launch_contract_tc(f16 != 0, maps, p->d_tc_works, p->d_tc_units,
+        cudaError_t e = launch_contract_tc(f16 != 0, maps, p->kb_rows32, 0, p->kb_rows16, p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
-                                           p->chunk_kb, part, p->d_err, st);
+                                           p->chunk_kb, part, p->d_err, (unsigned*)p->d_err + 1, st);
         if (e != cudaSuccess) return cuda_fail(e, "contract (modal, tensor cores)");
         ++launches;
         if (p->need_u) {
-            e = launch_contract_tc(f16 != 0, maps2, p->d_tcu_works, p->d_tcu_units,
+            e = launch_contract_tc(f16 != 0, maps, p->kb_rows32, nf, p->kb_rows16, p->d_tcu_works, p->d_tcu_units,
                                    (int)p->tc_u_sched.units.size(), p->tc_u_sched.lsup, p->tc_u_sched.nsup,
                                    p->d_tcu_pairs, p->slot2 * nf, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
-                                   p->chunk_kb, upart, p->d_err, st);
+                                   p->chunk_kb, upart, p->d_err, (unsigned*)p->d_err + 2, st);
             if (e != cudaSuccess) return cuda_fail(e, "contract (modal U, tensor cores)");
             ++launches;
         }

@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
                                                 size_t out_stride, uint32_t* __restrict__ hi,
                                                 uint32_t* __restrict__ lo, int f16,
                                                 const unsigned* __restrict__ fmax2,
-                                                unsigned* __restrict__ f0max) {
+                                                unsigned* __restrict__ f0max, FieldLayout lay) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = NN ? NN : g.n, M = N / 2;
     cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
@@ -396,10 +396,11 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
     if constexpr (NN > 0) res = fft_ct<R, false, P, NN / 2>(buf, scr, tw, 2);
     else res = fft_pingpong<R, false, P>(buf, scr, M, g.rad_h, g.nrad_h, tw, 2);
     const FieldDesc fd = fields[blockIdx.y];
-    R* dst = fd.out32 >= 0 ? out + (size_t)fd.out32 * out_stride : nullptr;
+    const bool kbm = lay.rows16 > 0;
+    R* dst = fd.out32 >= 0 ? out + (kbm ? (size_t)fd.out32 * 64 : (size_t)fd.out32 * out_stride) : nullptr;
     const size_t plane = (size_t)N * N * M;   // 32-bit words (two 16-bit values) per field plane
-    uint32_t* dhi = (fd.out16 >= 0 && hi) ? hi + (size_t)fd.out16 * plane : nullptr;
-    uint32_t* dlo = (fd.out16 >= 0 && lo) ? lo + (size_t)fd.out16 * plane : nullptr;
+    uint32_t* dhi = (fd.out16 >= 0 && hi) ? hi + (kbm ? (size_t)fd.out16 * 32 : (size_t)fd.out16 * plane) : nullptr;
+    uint32_t* dlo = (fd.out16 >= 0 && lo) ? lo + (kbm ? (size_t)fd.out16 * 32 : (size_t)fd.out16 * plane) : nullptr;
     // |F(x,y,z)| <= sum_kz 2 |H_kz| <= 2 nKz max|T2|: the split planes are
     // scaled by the power of two that keeps that bound below 2^15
     const float bound = fmax2 && fd.out16 >= 0 ? 2.f * (float)g.nKz * __uint_as_float(fmax2[fd.out16]) : 0.f;
@@ -410,10 +411,14 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
     for (int e = threadIdx.x; e < M * P; e += NTHR) {
         const int m = e % M, p = e / M, y = y0 + p;
         if (y >= N) continue;
+        // pos counts pairs of consecutive z (one complex, one 32-bit plane word);
+        // K-block-major: K-block pos / 32, word pos % 32 of its row
         const size_t pos = ((size_t)x * N + y) * M + m;
+        const size_t p32 = kbm ? (pos >> 5) * (size_t)lay.rows32 * 32 + (pos & 31) : pos;
+        const size_t p16 = kbm ? (pos >> 5) * (size_t)lay.rows16 * 32 + (pos & 31) : pos;
         const cx<R> v = res[sidx<false, P>(p, m, M)];
         if (dst) {
-            reinterpret_cast<cx<R>*>(dst)[pos] = cx<R>{v.re * s7, v.im * s7};
+            reinterpret_cast<cx<R>*>(dst)[p32] = cx<R>{v.re * s7, v.im * s7};
             if (f0max) mx = fmaxf(mx, fmaxf(fabsf((float)v.re), fabsf((float)v.im)));
         }
         if (dhi) {
@@ -434,8 +439,8 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
             const float r0 = x0 - h0, r1 = x1 - h1;
             if (f16) asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(r1), "f"(r0));
             else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(r1), "f"(r0));
-            dhi[pos] = h;
-            if (dlo) dlo[pos] = l;
+            dhi[p16] = h;
+            if (dlo) dlo[p16] = l;
         }
     }
     if (f0max && dst) block_max_to(f0max + fd.out32, mx);
@@ -458,7 +463,7 @@ template <typename R, int NN>
 cudaError_t launch_n(const FftGeom& g, const cx<float>* delta, const int16_t* shell_of, const float* radial,
                      const FieldDesc* d_fields, int nfields, const cx<R>* tw, cx<R>* t1, cx<R>* t2, R* out,
                      size_t out_stride, uint32_t* hi, uint32_t* lo, int f16, unsigned* fmax2, unsigned* f0max,
-                     cudaStream_t st) {
+                     cudaStream_t st, FieldLayout lay) {
     using C = FftCfg<R>;
     const int N = g.n, M = N / 2;
     const size_t t1_stride = (size_t)g.nK * N * g.nKz;
@@ -488,7 +493,7 @@ cudaError_t launch_n(const FftGeom& g, const cx<float>* delta, const int16_t* sh
     k_pass1<R, C::P, NN><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);
     k_pass2<R, C::P, NN><<<g2, NTHR, sm12, st>>>(g, t1, t1_stride, tw, t2, t2_stride, d_fields, fmax2);
     k_pass3<R, C::P3, NN><<<g3, NTHR, sm3, st>>>(g, t2, t2_stride, tw, d_fields, out, out_stride, hi, lo, f16,
-                                                 fmax2, f0max);
+                                                 fmax2, f0max, lay);
     return cudaGetLastError();
 }
 
@@ -501,11 +506,11 @@ cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const in
                               const float* radial, const FieldDesc* d_fields, int nfields,
                               const cx<R>* tw, cx<R>* t1, cx<R>* t2, R* out, size_t out_stride,
                               uint32_t* hi, uint32_t* lo, int f16, unsigned* fmax2, unsigned* f0max,
-                              cudaStream_t st) {
+                              cudaStream_t st, FieldLayout lay) {
 #define BSP_FFT_CASE(NV) \
     case NV:             \
         return launch_n<R, NV>(g, delta, shell_of, radial, d_fields, nfields, tw, t1, t2, out, out_stride, hi, lo, \
-                               f16, fmax2, f0max, st);
+                               f16, fmax2, f0max, st, lay);
     switch (g.n) {
         BSP_FFT_CASE(64)
         BSP_FFT_CASE(96)
@@ -515,7 +520,7 @@ cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const in
         BSP_FFT_CASE(512)
         default:
             return launch_n<R, 0>(g, delta, shell_of, radial, d_fields, nfields, tw, t1, t2, out, out_stride, hi, lo,
-                                  f16, fmax2, f0max, st);
+                                  f16, fmax2, f0max, st, lay);
     }
 #undef BSP_FFT_CASE
 }
@@ -523,10 +528,10 @@ cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const in
 template cudaError_t launch_fft_fields<float>(const FftGeom&, const cx<float>*, const int16_t*, const float*,
                                               const FieldDesc*, int, const cx<float>*, cx<float>*,
                                               cx<float>*, float*, size_t, uint32_t*, uint32_t*, int, unsigned*, unsigned*,
-                                              cudaStream_t);
+                                              cudaStream_t, FieldLayout);
 template cudaError_t launch_fft_fields<double>(const FftGeom&, const cx<float>*, const int16_t*, const float*,
                                                const FieldDesc*, int, const cx<double>*, cx<double>*,
                                                cx<double>*, double*, size_t, uint32_t*, uint32_t*, int,
-                                               unsigned*, unsigned*, cudaStream_t);
+                                               unsigned*, unsigned*, cudaStream_t, FieldLayout);
 
 }  // namespace bsp

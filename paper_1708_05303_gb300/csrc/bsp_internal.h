@@ -86,13 +86,24 @@ struct BinLoc {   // where T of (l, bin) lives in the partial buffer
     int pad;      // number of partial slots to sum when the caller passes nsplit <= 0
 };
 
+// Output layout of the real fields.  Field-major (rows32 = rows16 = 0):
+// field f at out + f * out_stride (FP32/FP64) and at plane f of hi/lo.
+// K-block-major (the tensor-core operands): x is cut into K-blocks of 64
+// points and K-block kb of field f sits at row kb * rows + f of a
+// [K-blocks * rows][64] array (rows32 for the FP32 output, rows16 for the
+// 16-bit planes), so that one K-block of every field is contiguous.
+struct FieldLayout {
+    int rows32 = 0;
+    int rows16 = 0;
+};
+
 // ---- launchers (bsp_fft.cu) ----
 template <typename R>
 cudaError_t launch_fft_fields(const FftGeom& g, const cx<float>* delta, const int16_t* shell_of,
                               const float* radial, const FieldDesc* d_fields, int nfields,
                               const cx<R>* tw, cx<R>* t1, cx<R>* t2, R* out, size_t out_stride,
                               uint32_t* hi, uint32_t* lo, int f16, unsigned* fmax2, unsigned* f0max,
-                              cudaStream_t st);
+                              cudaStream_t st, FieldLayout lay = FieldLayout());
 
 // Shot-noise combination in the reduction: v -= sum_t coef[t] * (sum of partial set t).
 struct ShotTerms {
@@ -126,10 +137,13 @@ struct TcMaps {
 };
 
 size_t tc_smem_bytes();
-cudaError_t launch_contract_tc(bool f16, const TcMaps& maps, const TcWork* works, const TcUnit* units, int nunits,
+// Fields in the K-block-major layout: F0 row of shell s in K-block kb at
+// kb * f0_rows + f0_row0 + s, field row f at kb * plane_rows + f.
+cudaError_t launch_contract_tc(bool f16, const TcMaps& maps, int f0_rows, int f0_row0, int plane_rows,
+                               const TcWork* works, const TcUnit* units, int nunits,
                                int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
-                               cudaStream_t st);
+                               unsigned* pace, cudaStream_t st);
 
 // ---- launchers (bsp_modal.cu) ----
 cudaError_t launch_modal_assemble(const double* T, const double* U, const int* ells, int n_ell, int nf,

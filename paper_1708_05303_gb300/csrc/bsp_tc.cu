@@ -203,6 +203,18 @@ __device__ __forceinline__ void unpack64(uint64_t v, float& x0, float& x1) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(v));
 }
 
+// Wait until *ctr >= target (acquire); false after ~4 s.
+__device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target) {
+    const long long t0 = clock64();
+    while (true) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) return true;
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+        __nanosleep(64);
+    }
+}
+
 __device__ __forceinline__ void set_abort(TcSmem& S, int* err, int code) {
     S.abort = 1;
     atomicOr(err, code);
@@ -210,11 +222,12 @@ __device__ __forceinline__ void set_abort(TcSmem& S, int* err, int code) {
 
 template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_contract_tc(const __grid_constant__ TcMaps maps, const TcWork* __restrict__ works,
+    k_contract_tc(const __grid_constant__ TcMaps maps, int f0_rows, int f0_row0, int plane_rows,
+                  const TcWork* __restrict__ works,
                   const int2* __restrict__ pair_shells, int pair_base,
                   const unsigned* __restrict__ fmax2, float bound_mul, const TcUnit* __restrict__ units,
                   int lsup, int nsup, int nprod, int CHUNK, double* __restrict__ partial,
-                  int* __restrict__ err) {
+                  int* __restrict__ err, unsigned* __restrict__ pace, int drift) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -312,21 +325,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     set_abort(S, err, 1);
                     break;
                 }
+                const int sup = k / unit.len, kin = k % unit.len;
+                // pacing: super-segment sup starts once every CTA has issued the loads
+                // of super-segments < sup - drift, so that works whose K-blocks cost
+                // different times still read the same fields while they sit in L2
+                if (pace && kin == 0 && sup > drift && !wait_count(pace, (unsigned)(gridDim.x * (sup - drift)))) {
+                    set_abort(S, err, 128);
+                    break;
+                }
                 mbar_expect_tx(&S.tma_full[s], bytes);
-                const int x0 = ((k / unit.len) * lsup + unit.start + k % unit.len) * TC_KB;
+                // K-block-major fields: K-block kb of row r is row kb * rows + r of a [.][64] array
+                const int kb = sup * lsup + unit.start + kin;
+                const int r0 = kb * f0_rows + f0_row0 + w.shell_lo, p0 = kb * plane_rows;
                 for (int h = 0; h < 2; ++h)
                     for (int m = TC_F0_MAPS - 1, off = 0; m >= 0; --m)
                         if (nfb - off >= (1 << m)) {
-                            tma_load_2d(&S.f0[s][h][off * 8 * 32], &maps.f0[m], x0 + 32 * h, w.shell_lo + 8 * off,
-                                        &S.tma_full[s]);
+                            tma_load_2d(&S.f0[s][h][off * 8 * 32], &maps.f0[m], 32 * h, r0 + 8 * off, &S.tma_full[s]);
                             off += 1 << m;
                         }
                 for (int j = 0; j < npc; ++j) {
                     const int4 c = S.pc[j];
-                    tma_load_2d(&S.b_hi[s][c.z * 1024], &maps.hi[c.x], x0, c.y, &S.tma_full[s]);
-                    if (two) tma_load_2d(&S.b_lo[s][c.z * 1024], &maps.lo[c.x], x0, c.y, &S.tma_full[s]);
+                    tma_load_2d(&S.b_hi[s][c.z * 1024], &maps.hi[c.x], 0, p0 + c.y, &S.tma_full[s]);
+                    if (two) tma_load_2d(&S.b_lo[s][c.z * 1024], &maps.lo[c.x], 0, p0 + c.y, &S.tma_full[s]);
                 }
                 issued = k + 1;
+                if (pace && kin == unit.len - 1) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(pace) : "memory");
             }
             // copies in flight must land before the CTA can exit: the last use of each stage
             for (int k = max(0, issued - NT); k < issued; ++k)
@@ -473,34 +496,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
-cudaError_t launch_contract_tc(bool f16, const TcMaps& maps, const TcWork* works, const TcUnit* units, int nunits,
+cudaError_t launch_contract_tc(bool f16, const TcMaps& maps, int f0_rows, int f0_row0, int plane_rows,
+                               const TcWork* works, const TcUnit* units, int nunits,
                                int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
-                               cudaStream_t st) {
+                               unsigned* pace, cudaStream_t st) {
     const size_t smem = tc_smem_bytes();
     static bool set16 = false, setb = false;   // once per kernel, never inside a graph capture
+    static int resident = -1;                  // CTAs that fit on the device at once
+    auto kern = f16 ? k_contract_tc<true> : k_contract_tc<false>;
     cudaError_t e;
-    if (f16) {
-        if (!set16) {
-            if ((e = cudaFuncSetAttribute(k_contract_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem)) != cudaSuccess)
-                return e;
-            set16 = true;
-        }
-        k_contract_tc<true><<<nunits, TC_THREADS, smem, st>>>(maps, works, pair_shells, pair_base, fmax2, bound_mul,
-                                                              units, lsup, nsup, nprod, chunk_kb, partial, err);
-    } else {
-        if (!setb) {
-            if ((e = cudaFuncSetAttribute(k_contract_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem)) != cudaSuccess)
-                return e;
-            setb = true;
-        }
-        k_contract_tc<false><<<nunits, TC_THREADS, smem, st>>>(maps, works, pair_shells, pair_base, fmax2,
-                                                               bound_mul, units, lsup, nsup, nprod, chunk_kb,
-                                                               partial, err);
+    bool& set = f16 ? set16 : setb;
+    if (!set) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        set = true;
     }
-    return cudaGetLastError();
+    if (resident < 0) {
+        int dev = 0, nsm = 0, per = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TC_THREADS, smem)) != cudaSuccess)
+            return e;
+        resident = nsm * per;
+    }
+    // pacing needs every CTA resident at once: a cooperative launch guarantees it
+    const bool paced = pace != nullptr && nunits <= resident;
+    const int drift = 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nunits);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = paced ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    unsigned* pc = paced ? pace : nullptr;
+    return cudaLaunchKernelEx(&cfg, kern, maps, f0_rows, f0_row0, plane_rows, works, pair_shells, pair_base, fmax2, bound_mul, units, lsup, nsup,
+                              nprod, chunk_kb, partial, err, pc, drift);
 }
 
 }  // namespace bsp
