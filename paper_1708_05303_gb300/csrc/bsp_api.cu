@@ -1,7 +1,6 @@
 // bsp_api.cu -- the C ABI of libbsp (include/bsp.h): plan creation, argument
 // checks, workspace layout, scheduling of the contraction tiles, and the
 // host orchestration of filter -> inverse FFT -> contraction -> reduction.
-#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -233,7 +232,9 @@ void assign_units(TcSched& h, size_t npts, int nsm) {
     }
 }
 
-TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, int nsh, size_t npts, int nsm) {
+// Fields are numbered slot * pad + a (pad = nsh rounded up to 8) so that
+// every box of 8 fields is one group of the K-block-major 16-bit planes.
+TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, int pad, size_t npts, int nsm) {
     TcSched h;
     std::map<std::pair<int, int>, int> pidx;
     for (auto& t : bins) pidx[{t[1], t[2]}] = 0;
@@ -260,10 +261,11 @@ TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, i
             lo = std::min(lo, alo[j]); hi = std::max(hi, ahi[j]);
             ++j;
         }
+        lo &= ~7;   // boxes start on a group
         const int na = hi - lo + 1, nbs = (na + 7) / 8;
         std::vector<int> boxes;
         for (int si : out_slots)
-            for (int b = 0; b < nbs; ++b) boxes.push_back(si * nsh + lo + 8 * b);
+            for (int b = 0; b < nbs; ++b) boxes.push_back(si * pad + lo + 8 * b);
         const int work0 = (int)h.works.size();
         for (size_t b0 = 0; b0 < boxes.size(); b0 += 16) {
             TcWork w{};
@@ -293,66 +295,6 @@ TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, i
 }
 
 constexpr size_t TC_UNIT = 128 * 128;   // FP64 partial values per tensor-core CTA
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
-    return fn;
-}
-
-// 2-D map over rows x npts elements, box = box_x elements x box_rows rows.
-bsp_status encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, size_t esize, size_t rows, size_t npts,
-                      bool swizzle, unsigned box_x, unsigned box_rows) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) {
-        g_last_error = "cuTensorMapEncodeTiled unavailable";
-        return BSP_ECUDA;
-    }
-    cuuint64_t dims[2] = {(cuuint64_t)npts, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(npts * esize)};
-    cuuint32_t box[2] = {box_x, box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        g_last_error = "cuTensorMapEncodeTiled failed: " + std::to_string((int)r);
-        return BSP_ECUDA;
-    }
-    return BSP_OK;
-}
-
-// The tensor-core contraction's maps over the K-block-major operands: F0
-// rows [nkb * f0_rows][64] FP32 in boxes of 32 points x 8 << i rows, and the
-// 16-bit planes [nkb * plane_rows][64] in boxes of 64 points x 8 << i rows,
-// all 128-byte swizzled (lo = hi for one product).
-bsp_status encode_tc_maps(TcMaps* m, float* f0, size_t f0_rows, void* hi, void* lo, size_t plane_rows, size_t nkb,
-                          bool f16) {
-    const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    bsp_status s;
-    for (int i = 0; i < TC_F0_MAPS; ++i)
-        if ((s = encode_map(&m->f0[i], f0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nkb * f0_rows, 64, true, 32,
-                            8u << i)) != BSP_OK)
-            return s;
-    for (int i = 0; i < TC_PLANE_MAPS; ++i)
-        if ((s = encode_map(&m->hi[i], hi, t16, 2, nkb * plane_rows, 64, true, 64, 8u << i)) != BSP_OK ||
-            (s = encode_map(&m->lo[i], lo ? lo : hi, t16, 2, nkb * plane_rows, 64, true, 64, 8u << i)) != BSP_OK)
-            return s;
-    return BSP_OK;
-}
 
 }  // namespace
 
@@ -437,7 +379,9 @@ struct bsp_plan {
     }
     size_t npts() const { return (size_t)n * n * n; }
     size_t nkb() const { return (npts() + 63) / 64; }   // K-blocks of 64 points
-    int kb_rows32 = 0, kb_rows16 = 0;   // rows per K-block of the tensor-core operands
+    // tensor-core operands (K-block-major): F0 rows per K-block; 16-bit fields are
+    // numbered slot * pad16 + a and stored in groups16 groups of 8 per K-block
+    int kb_rows32 = 0, pad16 = 0, groups16 = 0;
     int nslot() const { return (int)slot_ell.size(); }
 };
 
@@ -606,11 +550,14 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     }
     std::vector<FieldDesc> fdd, fdu;
     std::vector<FieldDesc> fdt;
+    const int pad16 = (n_shells + 7) & ~7;
+    p->pad16 = pad16;
+    p->groups16 = p->nslot() * pad16 / 8;
     for (int s = 0; s < p->nslot(); ++s)
         for (int a = 0; a < n_shells; ++a) {
             const int f = s * n_shells + a;
             fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, f, -1, {0, 0, 0}});
-            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, s == 0 ? a : -1, f, {0, 0, 0}});
+            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, s == 0 ? a : -1, s * pad16 + a, {0, 0, 0}});
         }
     if (p->shot) {
         // S^l_a = w_l |delta|^2 on a, then W^l_a = w_l on a (W^0 = the unit fields I)
@@ -627,7 +574,7 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
         (st = upload(&p->d_tw64, tw64)) != BSP_OK || (st = upload(&p->d_fd_delta, fdd)) != BSP_OK ||
         (st = upload(&p->d_fd_unit, fdu)) != BSP_OK || (st = upload(&p->d_fd_tc, fdt)) != BSP_OK ||
         (st = upload(&p->d_err, std::vector<int>{0, 0, 0})) != BSP_OK ||
-        (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)(p->nslot() + 1) * n_shells, 0u))) != BSP_OK) {
+        (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)p->nslot() * pad16 + n_shells, 0u))) != BSP_OK) {
         delete p;
         return st;
     }
@@ -665,14 +612,9 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     p->tout_bytes = round256(p->ells.size() * p->cand.size() * sizeof(double));
     if (p->tc) {
         p->kb_rows32 = n_shells;
-        p->kb_rows16 = (int)nfields32;
-        if ((double)p->nkb() * (double)(p->kb_rows16 + n_shells) >= 2147483647.0) {   // TMA coordinates are 32-bit
-            delete p;
-            return BSP_EUNSUPPORTED;
-        }
-        p->f0_bytes = round256((size_t)n_shells * p->nkb() * 64 * sizeof(float));
-        p->plane_bytes = round256(nfields32 * p->nkb() * 64 * 2);
-        TcSched tb = build_tc_sched(p->cand, p->out_slots, n_shells, p->npts(), p->nsm);
+        p->f0_bytes = round256((size_t)n_shells * p->nkb() * 256);
+        p->plane_bytes = round256((size_t)p->groups16 * p->nkb() * 1024);   // hi and lo: 2 * plane_bytes
+        TcSched tb = build_tc_sched(p->cand, p->out_slots, pad16, p->npts(), p->nsm);
         p->tc_part_bytes = round256(std::max<size_t>((size_t)p->nsm, tb.units.size()) * TC_UNIT * sizeof(double));
     }
     p->cnt_out_bytes = round256(p->cand.size() * sizeof(double));
@@ -763,6 +705,8 @@ bsp_status bsp_plan_create_modal(bsp_plan** out, int n, double box, int n_funcs,
     // FP32 copies are the pair factors: slot 0, then slot2 (for U) at index nf + a
     const int nf = n_funcs;
     std::vector<FieldDesc> fdd, fdt;
+    p->pad16 = (nf + 7) & ~7;
+    p->groups16 = p->nslot() * p->pad16 / 8;
     for (int s = 0; s < p->nslot(); ++s)
         for (int a = 0; a < nf; ++a) {
             const int f = s * nf + a;
@@ -770,14 +714,14 @@ bsp_status bsp_plan_create_modal(bsp_plan** out, int n, double box, int n_funcs,
             int o32 = -1;
             if (s == 0) o32 = a;
             else if (p->need_u && s == p->slot2) o32 = nf + a;
-            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_RADIAL, o32, f, {0, 0, 0}});
+            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_RADIAL, o32, s * p->pad16 + a, {0, 0, 0}});
         }
     bsp_status st;
     if ((st = upload(&p->d_radial, tab)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||
         (st = upload(&p->d_tw64, tw64)) != BSP_OK || (st = upload(&p->d_fd_delta, fdd)) != BSP_OK ||
         (st = upload(&p->d_fd_tc, fdt)) != BSP_OK || (st = upload(&p->d_err, std::vector<int>{0, 0, 0})) != BSP_OK ||
         (st = upload(&p->d_ells, p->ells)) != BSP_OK ||
-        (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)(p->nslot() + 2) * nf, 0u))) != BSP_OK) {
+        (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)p->nslot() * p->pad16 + 2 * nf, 0u))) != BSP_OK) {
         delete p;
         return st;
     }
@@ -810,15 +754,10 @@ bsp_status bsp_plan_create_modal(bsp_plan** out, int n, double box, int n_funcs,
             }
         }
     } else {
-        p->tc_sched = build_tc_sched(p->bins, p->out_slots, nf, p->npts(), p->nsm);
+        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->pad16, p->npts(), p->nsm);
         p->kb_rows32 = (p->need_u ? 2 : 1) * nf;
-        p->kb_rows16 = (int)nfields;
-        if ((double)p->nkb() * (double)(p->kb_rows16 + p->kb_rows32) >= 2147483647.0) {
-            delete p;
-            return BSP_EUNSUPPORTED;
-        }
-        p->f0_bytes = round256((size_t)p->kb_rows32 * p->nkb() * 64 * sizeof(float));
-        p->plane_bytes = round256(nfields * p->nkb() * 64 * 2);
+        p->f0_bytes = round256((size_t)p->kb_rows32 * p->nkb() * 256);
+        p->plane_bytes = round256((size_t)p->groups16 * p->nkb() * 1024);   // hi and lo: 2 * plane_bytes
         p->tc_part_bytes = round256(p->tc_sched.units.size() * TC_UNIT * sizeof(double));
         if ((st = upload(&p->d_tc_units, p->tc_sched.units)) != BSP_OK ||
             (st = upload(&p->d_tc_works, p->tc_sched.works)) != BSP_OK ||
@@ -828,7 +767,7 @@ bsp_status bsp_plan_create_modal(bsp_plan** out, int n, double box, int n_funcs,
             return st;
         }
         if (p->need_u) {
-            p->tc_u_sched = build_tc_sched(p->bins, std::vector<int>{0}, nf, p->npts(), p->nsm);
+            p->tc_u_sched = build_tc_sched(p->bins, std::vector<int>{0}, p->pad16, p->npts(), p->nsm);
             p->tcu_part_bytes = round256(p->tc_u_sched.units.size() * TC_UNIT * sizeof(double));
             if ((st = upload(&p->d_tcu_units, p->tc_u_sched.units)) != BSP_OK ||
                 (st = upload(&p->d_tcu_works, p->tc_u_sched.works)) != BSP_OK ||
@@ -880,7 +819,7 @@ static bsp_status finish_counts(bsp_plan* p) {
     bsp_status s = upload_sched(p->comp_dev, p->comp_sched);
     if (s != BSP_OK) return s;
     if (p->tc) {
-        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->nsh, p->npts(), p->nsm);
+        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->pad16, p->npts(), p->nsm);
         if (round256(p->tc_sched.units.size() * TC_UNIT * sizeof(double)) > p->tc_part_bytes) return BSP_ENOMEM;
         cudaFree(p->d_tc_works); cudaFree(p->d_tc_pairs); cudaFree(p->d_tc_loc); cudaFree(p->d_tc_units);
         p->d_tc_works = nullptr; p->d_tc_pairs = nullptr; p->d_tc_loc = nullptr; p->d_tc_units = nullptr;
@@ -971,6 +910,16 @@ static bsp_status mark(bsp_plan* p, cudaStream_t st, int k) {
     return BSP_OK;
 }
 
+// The last K-block of the tensor-core operands is partly past the grid when
+// n^3 is not a multiple of 64: zero it before the FFT fills the rest.
+static bsp_status clear_tail(bsp_plan* p, float* f0, uint32_t* planes, cudaStream_t st) {
+    if (p->npts() % 64 == 0) return BSP_OK;
+    const size_t kb = p->nkb() - 1;
+    CK(cudaMemsetAsync((char*)f0 + kb * p->kb_rows32 * 256, 0, (size_t)p->kb_rows32 * 256, st));
+    CK(cudaMemsetAsync((char*)planes + kb * p->groups16 * 2048, 0, (size_t)p->groups16 * 2048, st));
+    return BSP_OK;
+}
+
 static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, void* ws, cudaStream_t st,
                                double* B) {
     if (nbar != 0.0 && !p->shot) return p->tc ? BSP_EUNSUPPORTED : BSP_EINVAL;
@@ -982,33 +931,29 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
     char* base = (char*)ws;
     if (p->tc) {
         float* f0 = (float*)(base + L.fields);
-        uint32_t* hi = (uint32_t*)(base + L.fields + p->f0_bytes);
-        uint32_t* lo = (uint32_t*)(base + L.fields + p->f0_bytes + p->plane_bytes);
+        uint32_t* hi = (uint32_t*)(base + L.fields + p->f0_bytes);   // hi and lo, K-block-major groups
         cx<float>* t1 = (cx<float>*)(base + L.t1);
         cx<float>* t2 = (cx<float>*)(base + L.t2);
         const int nf = p->nslot() * p->nsh;
-        unsigned* fmax2 = p->d_fmax;              // [nf]  max |T2| per field (bounds |F|)
-        CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * (nf + p->nsh), st));
+        unsigned* fmax2 = p->d_fmax;              // [slot * pad16 + a]  max |T2| per field (bounds |F|)
+        CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * ((size_t)p->nslot() * p->pad16 + p->nsh), st));
         CK(cudaMemsetAsync(p->d_err, 0, 3 * sizeof(int), st));   // error code, pacing counters
+        if ((ms = clear_tail(p, f0, hi, st)) != BSP_OK) return ms;
         const int f16 = p->prec == BSP_SPLIT_F16 ? 1 : 0;
         for (int f0i = 0; f0i < nf; f0i += p->fb32) {
             int nb = std::min(p->fb32, nf - f0i);
             cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, p->d_shell_of, nullptr,
                                                      p->d_fd_tc + f0i, nb, p->d_tw32, t1, t2, f0, p->npts(), hi,
-                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, nullptr, st,
-                                                     FieldLayout{p->kb_rows32, p->kb_rows16});
+                                                     p->nprod == 3 ? hi : nullptr, f16, fmax2, nullptr, st,
+                                                     FieldLayout{p->kb_rows32, p->groups16});
             if (e != cudaSuccess) return cuda_fail(e, "fft");
             launches += 3;
         }
         if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
-        TcMaps maps;
-        bsp_status es;
-        if ((es = encode_tc_maps(&maps, f0, p->kb_rows32, hi, p->nprod == 3 ? lo : nullptr, p->kb_rows16, p->nkb(),
-                                 f16 != 0)) != BSP_OK)
-            return es;
         double* partial = (double*)(base + L.partial);
         double* tout = (double*)(base + L.tout);
-        cudaError_t e = launch_contract_tc(f16 != 0, maps, p->kb_rows32, 0, p->kb_rows16, p->d_tc_works, p->d_tc_units,
+        cudaError_t e = launch_contract_tc(f16 != 0, f0, p->kb_rows32, 0, hi, p->groups16, (long long)p->nkb(),
+                                           p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
                                            p->chunk_kb, partial, p->d_err, (unsigned*)p->d_err + 1, st);
@@ -1132,40 +1077,37 @@ bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* s
     } else {
         float* f0 = (float*)(base + L.fields);
         uint32_t* hi = (uint32_t*)(base + L.fields + p->f0_bytes);
-        uint32_t* lo = (uint32_t*)(base + L.fields + p->f0_bytes + p->plane_bytes);
         cx<float>* t1 = (cx<float>*)(base + L.t1);
         cx<float>* t2 = (cx<float>*)(base + L.t2);
-        unsigned* fmax2 = p->d_fmax;                    // [nfields] max |T2| per field (bounds |F|)
-        CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * (nfields + 2 * nf), st));
+        unsigned* fmax2 = p->d_fmax;                    // [slot * pad16 + a] max |T2| per field (bounds |F|)
+        CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * ((size_t)p->nslot() * p->pad16 + 2 * nf), st));
         CK(cudaMemsetAsync(p->d_err, 0, 3 * sizeof(int), st));   // error code, pacing counters
+        if ((ms = clear_tail(p, f0, hi, st)) != BSP_OK) return ms;
         const int f16 = p->prec == BSP_SPLIT_F16 ? 1 : 0;
         for (int fi = 0; fi < nfields; fi += p->fb32) {
             const int nb = std::min(p->fb32, nfields - fi);
             cudaError_t e = launch_fft_fields<float>(p->geom, (const cx<float>*)delta_k, nullptr, p->d_radial,
                                                      p->d_fd_tc + fi, nb, p->d_tw32, t1, t2, f0, p->npts(), hi,
-                                                     p->nprod == 3 ? lo : nullptr, f16, fmax2, nullptr, st,
-                                                     FieldLayout{p->kb_rows32, p->kb_rows16});
+                                                     p->nprod == 3 ? hi : nullptr, f16, fmax2, nullptr, st,
+                                                     FieldLayout{p->kb_rows32, p->groups16});
             if (e != cudaSuccess) return cuda_fail(e, "fft (modal)");
             launches += 3;
         }
         if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
-        TcMaps maps;
-        bsp_status es;
-        if ((es = encode_tc_maps(&maps, f0, p->kb_rows32, hi, p->nprod == 3 ? lo : nullptr, p->kb_rows16, p->nkb(),
-                                 f16 != 0)) != BSP_OK)
-            return es;
         double* part = (double*)(base + L.partial);
         double* upart = (double*)(base + L.partial + p->tc_part_bytes);
-        cudaError_t e = launch_contract_tc(f16 != 0, maps, p->kb_rows32, 0, p->kb_rows16, p->d_tc_works, p->d_tc_units,
+        cudaError_t e = launch_contract_tc(f16 != 0, f0, p->kb_rows32, 0, hi, p->groups16, (long long)p->nkb(),
+                                           p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
                                            p->chunk_kb, part, p->d_err, (unsigned*)p->d_err + 1, st);
         if (e != cudaSuccess) return cuda_fail(e, "contract (modal, tensor cores)");
         ++launches;
         if (p->need_u) {
-            e = launch_contract_tc(f16 != 0, maps, p->kb_rows32, nf, p->kb_rows16, p->d_tcu_works, p->d_tcu_units,
+            e = launch_contract_tc(f16 != 0, f0, p->kb_rows32, nf, hi, p->groups16, (long long)p->nkb(),
+                                   p->d_tcu_works, p->d_tcu_units,
                                    (int)p->tc_u_sched.units.size(), p->tc_u_sched.lsup, p->tc_u_sched.nsup,
-                                   p->d_tcu_pairs, p->slot2 * nf, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
+                                   p->d_tcu_pairs, p->slot2 * p->pad16, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
                                    p->chunk_kb, upart, p->d_err, (unsigned*)p->d_err + 2, st);
             if (e != cudaSuccess) return cuda_fail(e, "contract (modal U, tensor cores)");
             ++launches;

@@ -396,11 +396,21 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
     if constexpr (NN > 0) res = fft_ct<R, false, P, NN / 2>(buf, scr, tw, 2);
     else res = fft_pingpong<R, false, P>(buf, scr, M, g.rad_h, g.nrad_h, tw, 2);
     const FieldDesc fd = fields[blockIdx.y];
-    const bool kbm = lay.rows16 > 0;
-    R* dst = fd.out32 >= 0 ? out + (kbm ? (size_t)fd.out32 * 64 : (size_t)fd.out32 * out_stride) : nullptr;
+    const bool kbm = lay.groups16 > 0;
+    R* dst = fd.out32 >= 0 ? out + (kbm ? (size_t)0 : (size_t)fd.out32 * out_stride) : nullptr;
     const size_t plane = (size_t)N * N * M;   // 32-bit words (two 16-bit values) per field plane
-    uint32_t* dhi = (fd.out16 >= 0 && hi) ? hi + (kbm ? (size_t)fd.out16 * 32 : (size_t)fd.out16 * plane) : nullptr;
-    uint32_t* dlo = (fd.out16 >= 0 && lo) ? lo + (kbm ? (size_t)fd.out16 * 32 : (size_t)fd.out16 * plane) : nullptr;
+    uint32_t* dhi = nullptr;
+    uint32_t* dlo = nullptr;
+    if (fd.out16 >= 0 && hi) {
+        if (kbm) {   // hi rows of the field's group, lo rows 1024 bytes further
+            dhi = hi + (size_t)(fd.out16 >> 3) * 512 + (size_t)(fd.out16 & 7) * 32;
+            dlo = lo ? dhi + 256 : nullptr;
+        } else {
+            dhi = hi + (size_t)fd.out16 * plane;
+            dlo = lo ? lo + (size_t)fd.out16 * plane : nullptr;
+        }
+    }
+    const int r32 = fd.out32 & 7, r16 = fd.out16 & 7;
     // |F(x,y,z)| <= sum_kz 2 |H_kz| <= 2 nKz max|T2|: the split planes are
     // scaled by the power of two that keeps that bound below 2^15
     const float bound = fmax2 && fd.out16 >= 0 ? 2.f * (float)g.nKz * __uint_as_float(fmax2[fd.out16]) : 0.f;
@@ -412,10 +422,16 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
         const int m = e % M, p = e / M, y = y0 + p;
         if (y >= N) continue;
         // pos counts pairs of consecutive z (one complex, one 32-bit plane word);
-        // K-block-major: K-block pos / 32, word pos % 32 of its row
+        // K-block-major: K-block pos / 32, pair w = pos % 32 of it (points 2w, 2w+1)
         const size_t pos = ((size_t)x * N + y) * M + m;
-        const size_t p32 = kbm ? (pos >> 5) * (size_t)lay.rows32 * 32 + (pos & 31) : pos;
-        const size_t p16 = kbm ? (pos >> 5) * (size_t)lay.rows16 * 32 + (pos & 31) : pos;
+        size_t p32 = pos, p16 = pos;
+        if (kbm) {
+            const size_t kb = pos >> 5;
+            const int w = (int)(pos & 31);
+            const int J = w >> 1;   // 16-byte chunk of the 256-byte FP32 row
+            p32 = (kb * (size_t)lay.rows32 + (size_t)fd.out32) * 32 + (size_t)(((J & 8) | ((J & 7) ^ r32)) * 2 + (w & 1));
+            p16 = kb * (size_t)lay.groups16 * 512 + (size_t)((((w >> 2) ^ r16) << 2) | (w & 3));
+        }
         const cx<R> v = res[sidx<false, P>(p, m, M)];
         if (dst) {
             reinterpret_cast<cx<R>*>(dst)[p32] = cx<R>{v.re * s7, v.im * s7};

@@ -2,7 +2,6 @@
 // Not part of the public ABI (include/bsp.h is).
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -66,7 +65,7 @@ struct TcWork {
     int nbox;               // boxes of 8 consecutive field rows
     int n;                  // MMA N
     int pad[2];
-    int box_field[16];      // first field row of each box
+    int box_field[16];      // first field (plane index, a multiple of 8) of each box
 };
 
 // One persistent tensor-core CTA: the x-range is swept in super-segments of
@@ -86,15 +85,21 @@ struct BinLoc {   // where T of (l, bin) lives in the partial buffer
     int pad;      // number of partial slots to sum when the caller passes nsplit <= 0
 };
 
-// Output layout of the real fields.  Field-major (rows32 = rows16 = 0):
+// Output layout of the real fields.  Field-major (rows32 = groups16 = 0):
 // field f at out + f * out_stride (FP32/FP64) and at plane f of hi/lo.
-// K-block-major (the tensor-core operands): x is cut into K-blocks of 64
-// points and K-block kb of field f sits at row kb * rows + f of a
-// [K-blocks * rows][64] array (rows32 for the FP32 output, rows16 for the
-// 16-bit planes), so that one K-block of every field is contiguous.
+// K-block-major (the tensor-core operands; x is cut into K-blocks of 64
+// points, each stored as the shared-memory image the contraction copies):
+//   FP32: K-block kb of row r (= out32) is the 256-byte row kb * rows32 + r
+//         of a [K-blocks * rows32][64] array; 16-byte chunk J of a row sits
+//         at chunk (J & 8) | ((J & 7) ^ (r & 7)) (the 128-byte swizzle of
+//         each half);
+//   16-bit planes: fields come in groups of 8; K-block kb of group g is the
+//         2048 bytes at (kb * groups16 + g) * 2048 of `hi`: the 8 hi rows
+//         (128 bytes each) then the 8 lo rows, chunk j of row r at chunk
+//         j ^ r (the 128-byte swizzle of the tensor-core operand).
 struct FieldLayout {
     int rows32 = 0;
-    int rows16 = 0;
+    int groups16 = 0;
 };
 
 // ---- launchers (bsp_fft.cu) ----
@@ -125,22 +130,12 @@ cudaError_t launch_reduce(const double* partial, int nsplit, size_t unit, int ro
                           const ShotTerms* shot = nullptr);
 
 // ---- launchers (bsp_tc.cu) ----
-// Tensor maps of one tensor-core contraction, one per box height: F0 rows
-// (FP32, boxes of 32 points x 8 << i rows, 128-byte swizzle) and the 16-bit
-// hi / lo planes (boxes of 64 points x 8 << i rows, 128-byte swizzle).
-constexpr int TC_F0_MAPS = 4;      // 8, 16, 32, 64 rows
-constexpr int TC_PLANE_MAPS = 5;   // 8, 16, 32, 64, 128 rows
-struct TcMaps {
-    CUtensorMap f0[TC_F0_MAPS];
-    CUtensorMap hi[TC_PLANE_MAPS];
-    CUtensorMap lo[TC_PLANE_MAPS];
-};
-
+// Operands in the K-block-major layout (FieldLayout): F0 row of shell s in
+// K-block kb is row kb * f0_rows + f0_row0 + s of f0; the 16-bit planes have
+// `groups` groups of 8 fields per K-block; works name fields by plane index.
 size_t tc_smem_bytes();
-// Fields in the K-block-major layout: F0 row of shell s in K-block kb at
-// kb * f0_rows + f0_row0 + s, field row f at kb * plane_rows + f.
-cudaError_t launch_contract_tc(bool f16, const TcMaps& maps, int f0_rows, int f0_row0, int plane_rows,
-                               const TcWork* works, const TcUnit* units, int nunits,
+cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_row0, const uint32_t* planes,
+                               int groups, long long nkb, const TcWork* works, const TcUnit* units, int nunits,
                                int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
                                unsigned* pace, cudaStream_t st);

@@ -7,10 +7,11 @@
 // A CTA owns one tile -- 128 pairs (the MMA M) times N <= 128 field rows --
 // and one x-segment, and runs a warp-specialised pipeline per K-block of 64
 // points:
-//   warp 0      TMA: F^0 rows (FP32) of the tile's shells and the 16-bit
-//               hi/lo planes of its field rows, a few large 128-byte-swizzled
-//               boxes per K-block, four stages deep;
-//   warps 4-11  form P = F_b F_c in FP32 (one pair per TMEM lane, half a
+//   warp 0      bulk copies (TMA engine, no tensor map): the F^0 rows (FP32)
+//               of the tile's shells and the hi/lo planes of its field
+//               groups, stored by the FFT as the swizzled shared-memory image
+//               (one copy per contiguous run), four stages deep;
+//   warps 4-19  form P = F_b F_c in FP32 (one pair per TMEM lane, a quarter
 //               K-block per warp), split it into 16-bit hi + lo and store
 //               both in tensor memory, where the MMA reads its A operand;
 //   warp 1      one thread issues tcgen05.mma kind::f16, M=128, K=16, A from
@@ -18,7 +19,7 @@
 //               D += P_hi F_hi + P_hi F_lo + P_lo F_hi (split products;
 //               one product for the plain 16-bit mode), FP32 accumulators
 //               in tensor memory;
-//   warps 12-15 drain the accumulator every `chunk` K-blocks (tcgen05.ld),
+//   warps 20-23 drain the accumulator every `chunk` K-blocks (tcgen05.ld),
 //               add it to a running FP32 sum in tensor memory, and every
 //               FLUSH_KB K-blocks add that sum, unscaled, to the CTA's FP64
 //               slot in global memory.
@@ -26,7 +27,6 @@
 // CUDA-core prologue, the MMAs and the epilogue overlapped.  Every mbarrier
 // wait is bounded; on timeout the CTA records an error code, stops, waits
 // (bounded) for its own copies in flight and releases its tensor memory.
-#include <cuda.h>
 
 #include "bsp_internal.h"
 
@@ -39,8 +39,8 @@ constexpr int TC_NMAX = 128;     // field rows per tile = MMA N (max)
 constexpr int TC_KB = 64;        // x-points per K-block (128 bytes of 16-bit values)
 constexpr int NT = 4;            // TMA ring stages (F0 rows + field planes)
 constexpr int TC_MAXSH = 64;     // F0 rows per tile
-constexpr int TC_THREADS = 512;  // 16 warps
-constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, N_PRO = 8, W_EPI0 = 12;
+constexpr int TC_THREADS = 768;  // 24 warps
+constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, N_PRO = 16, W_EPI0 = 20;
 // tensor memory columns: acc0 [0,128) acc1 [128,256) running sum [256,384)
 // A buffers [384,448) and [448,512): hi in the first 32 columns, lo in the next 32
 constexpr uint32_t TMEM_COLS = 512, COL_SUM = 256, COL_A = 384;
@@ -48,14 +48,15 @@ constexpr int FLUSH_KB = 128;    // K-blocks between FP64 flushes of the running
 constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
 
 struct TcSmem {
-    float f0[NT][2][TC_MAXSH * 32];     // [stage][half of the K-block][row][32 points], swizzled
-    uint8_t b_hi[NT][TC_NMAX * 128];
-    uint8_t b_lo[NT][TC_NMAX * 128];
-    uint64_t tma_full[NT], tma_empty[NT], a_full[2], a_empty[2], acc_full[2], acc_empty[2];
+    uint8_t f0[NT][TC_MAXSH * 256];        // [stage][row][64 floats], each half 128-byte swizzled
+    uint8_t b[NT][TC_NMAX / 8 * 2048];     // [stage][group of 8 fields][hi 1024 B | lo 1024 B]
+    // tma_full: a stage's copies landed; kb_done: the MMAs of K-block k finished
+    // (frees TMA stage k % NT and A buffer k % 2); a_full: A buffer written
+    uint64_t tma_full[NT], kb_done[NT], a_full[2], acc_full[2], acc_empty[2];
     uint32_t tmem_base;
     volatile int abort;
     int npc;                  // plane copies per K-block
-    int4 pc[16];              // plane copy: (map, first field row, first box, -)
+    int4 pc[16];              // plane copy: (first group in the K-block, first group in the stage, groups, -)
     int2 pf[TC_M];
     float pscale[TC_M];
     float fscale[TC_NMAX];
@@ -77,8 +78,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 // Wait for the phase of parity `parity` to complete; false after ~4 s.
+__device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
     const uint32_t addr = smem_u32(b);
+    if (mbar_test(addr, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         uint32_t done;
@@ -93,12 +105,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int c0, int c1, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on bar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -134,16 +146,21 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
         "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
         : "memory");
 }
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand in 8-row x 128-byte atoms
-// with the 128-byte swizzle, atoms 1024 bytes apart (stride byte offset).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// with the 128-byte swizzle, atoms `sbo` bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address >> 4
     d |= (uint64_t)1 << 16;                     // leading byte offset (unused with this swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset >> 4
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;   // stride byte offset >> 4
     d |= (uint64_t)1 << 46;                     // descriptor version (0b001)
     d |= (uint64_t)2 << 61;                     // 128-byte swizzle
     return d;
@@ -222,8 +239,8 @@ __device__ __forceinline__ void set_abort(TcSmem& S, int* err, int code) {
 
 template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_contract_tc(const __grid_constant__ TcMaps maps, int f0_rows, int f0_row0, int plane_rows,
-                  const TcWork* __restrict__ works,
+    k_contract_tc(const float* __restrict__ gf0, int f0_rows, int f0_row0, const uint32_t* __restrict__ gplanes,
+                  int groups, long long nkb_real, const TcWork* __restrict__ works,
                   const int2* __restrict__ pair_shells, int pair_base,
                   const unsigned* __restrict__ fmax2, float bound_mul, const TcUnit* __restrict__ units,
                   int lsup, int nsup, int nprod, int CHUNK, double* __restrict__ partial,
@@ -247,37 +264,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (tid == 0) {
         for (int s = 0; s < NT; ++s) {
             mbar_init(&S.tma_full[s], 1);
-            mbar_init(&S.tma_empty[s], 1);
+            mbar_init(&S.kb_done[s], 1);
         }
         for (int j = 0; j < 2; ++j) {
             mbar_init(&S.a_full[j], N_PRO);
-            mbar_init(&S.a_empty[j], 1);
             mbar_init(&S.acc_full[j], 1);
             mbar_init(&S.acc_empty[j], 4);
         }
         S.abort = 0;
-        // field-plane copies: runs of consecutive 8-row boxes, split into
-        // boxes of 128, 64, 32, 16, 8 rows
+        // field-plane copies: one per run of consecutive groups
         int npc = 0;
         for (int j = 0; j < w.nbox;) {
             int L = 1;
             while (j + L < w.nbox && w.box_field[j + L] == w.box_field[j] + 8 * L) ++L;
-            for (int m = TC_PLANE_MAPS - 1, off = 0; m >= 0; --m)
-                while (L - off >= (1 << m)) {
-                    S.pc[npc++] = make_int4(m, w.box_field[j + off], j + off, 0);
-                    off += 1 << m;
-                }
+            S.pc[npc++] = make_int4(w.box_field[j] >> 3, j, L, 0);
             j += L;
         }
         S.npc = npc;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // MMA rows past the tile's boxes (N rounds 8 nbox up to 16) read zeros
-    for (int i = tid; i < NT * 2 * ((int)N - 8 * w.nbox) * 32; i += TC_THREADS) {
-        const int per = ((int)N - 8 * w.nbox) * 32, s = i / per, r = i % per;
-        uint8_t* base = (s & 1) ? S.b_lo[s >> 1] : S.b_hi[s >> 1];
-        reinterpret_cast<uint32_t*>(base + 8 * w.nbox * 128)[r] = 0u;
-    }
+    // zero every stage once: MMA rows past the tile's groups (N rounds 8 nbox up
+    // to 16) and K-blocks past the end of the grid (no copies) then read zeros
+    for (int i = tid; i < (int)(sizeof(S.f0) + sizeof(S.b)) / 16; i += TC_THREADS)
+        reinterpret_cast<uint4*>(S.f0)[i] = make_uint4(0u, 0u, 0u, 0u);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid < TC_M) {
         int2 v = {-1, -1};
@@ -314,14 +323,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (warp == W_TMA) {
         if (lane == 0) {
-            const int nfb = (w.nshell + 7) >> 3;   // 8-row F0 boxes per half K-block
             const int npc = S.npc;
-            const bool two = nprod == 3;
-            const uint32_t bytes = (uint32_t)nfb * 2048 + (uint32_t)w.nbox * 1024 * (two ? 2 : 1);
+            const uint32_t f0_bytes = (uint32_t)w.nshell * 256;
+            const uint32_t bytes = f0_bytes + (uint32_t)w.nbox * 2048;
+            const uint8_t* f0src = reinterpret_cast<const uint8_t*>(gf0) + (size_t)(f0_row0 + w.shell_lo) * 256;
+            const uint8_t* psrc = reinterpret_cast<const uint8_t*>(gplanes);
             int issued = 0;
             for (int k = 0; k < nkb && !S.abort; ++k) {
                 const int s = k % NT, u = k / NT;
-                if (u > 0 && !mbar_wait(&S.tma_empty[s], (u - 1) & 1)) {
+                if (u > 0 && !mbar_wait(&S.kb_done[s], (u - 1) & 1)) {
                     set_abort(S, err, 1);
                     break;
                 }
@@ -333,20 +343,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     set_abort(S, err, 128);
                     break;
                 }
-                mbar_expect_tx(&S.tma_full[s], bytes);
-                // K-block-major fields: K-block kb of row r is row kb * rows + r of a [.][64] array
-                const int kb = sup * lsup + unit.start + kin;
-                const int r0 = kb * f0_rows + f0_row0 + w.shell_lo, p0 = kb * plane_rows;
-                for (int h = 0; h < 2; ++h)
-                    for (int m = TC_F0_MAPS - 1, off = 0; m >= 0; --m)
-                        if (nfb - off >= (1 << m)) {
-                            tma_load_2d(&S.f0[s][h][off * 8 * 32], &maps.f0[m], 32 * h, r0 + 8 * off, &S.tma_full[s]);
-                            off += 1 << m;
-                        }
-                for (int j = 0; j < npc; ++j) {
-                    const int4 c = S.pc[j];
-                    tma_load_2d(&S.b_hi[s][c.z * 1024], &maps.hi[c.x], 0, p0 + c.y, &S.tma_full[s]);
-                    if (two) tma_load_2d(&S.b_lo[s][c.z * 1024], &maps.lo[c.x], 0, p0 + c.y, &S.tma_full[s]);
+                const long long kb = (long long)sup * lsup + unit.start + kin;
+                if (kb < nkb_real) {
+                    mbar_expect_tx(&S.tma_full[s], bytes);
+                    bulk_load(S.f0[s], f0src + (size_t)kb * f0_rows * 256, f0_bytes, &S.tma_full[s]);
+                    for (int j = 0; j < npc; ++j) {
+                        const int4 c = S.pc[j];
+                        bulk_load(&S.b[s][c.y * 2048], psrc + ((size_t)kb * groups + c.x) * 2048,
+                                  (uint32_t)c.z * 2048, &S.tma_full[s]);
+                    }
+                } else {
+                    mbar_expect_tx(&S.tma_full[s], 0);   // past the grid: nothing to load
                 }
                 issued = k + 1;
                 if (pace && kin == unit.len - 1) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(pace) : "memory");
@@ -358,62 +365,71 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == W_MMA) {
         if (lane == 0) {
             const uint32_t idesc = make_idesc(F16 ? 0u : 1u, N);
-            int done = 0;
-            for (int k = 0; k < nkb && !S.abort; ++k) {
-                const int s = k % NT, u = k / NT, sa = k & 1, ua = k >> 1;
-                const int c = k / CHUNK, j = c & 1;
-                const bool first = (k % CHUNK) == 0;
-                const bool last = (k % CHUNK) == CHUNK - 1 || k == nkb - 1;
-                if (first && c >= 2 && !mbar_wait(&S.acc_empty[j], ((c >> 1) - 1) & 1)) {
+            const uint32_t b0 = smem_u32(S.b[0]);
+            int done = 0, kc = 0, c = 0;   // kc = k % CHUNK, c = k / CHUNK
+            for (int k = 0; k < nkb; ++k) {
+                const int s = k % NT, u = k / NT, sa = k & 1;
+                const int j = c & 1;
+                if (kc == 0 && c >= 2 && !mbar_wait(&S.acc_empty[j], ((c >> 1) - 1) & 1)) {
                     set_abort(S, err, 2);
                     break;
                 }
-                if (!mbar_wait(&S.tma_full[s], u & 1) || !mbar_wait(&S.a_full[sa], ua & 1)) {
+                if (!mbar_wait(&S.tma_full[s], u & 1) || !mbar_wait(&S.a_full[sa], (k >> 1) & 1)) {
                     set_abort(S, err, 4);
                     break;
                 }
+                if (S.abort) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(j * 128);
                 const uint32_t ah = tmem + COL_A + (uint32_t)sa * 64, al = ah + 32;
-                const uint32_t bh = smem_u32(S.b_hi[s]), bl = smem_u32(S.b_lo[s]);
+                const uint32_t bh = b0 + (uint32_t)s * (uint32_t)sizeof(S.b[0]), bl = bh + 1024;
 #pragma unroll
                 for (int kk = 0; kk < TC_KB / 16; ++kk) {
                     const uint32_t o = (uint32_t)kk * 32, oa = (uint32_t)kk * 8;
-                    mma_ts(d, ah + oa, sw128_desc(bh + o), idesc, (first && kk == 0) ? 0u : 1u);
+                    mma_ts(d, ah + oa, sw128_desc(bh + o, 2048), idesc, (kc == 0 && kk == 0) ? 0u : 1u);
                     if (nprod == 3) {
-                        mma_ts(d, ah + oa, sw128_desc(bl + o), idesc, 1u);
-                        mma_ts(d, al + oa, sw128_desc(bh + o), idesc, 1u);
+                        mma_ts(d, ah + oa, sw128_desc(bl + o, 2048), idesc, 1u);
+                        mma_ts(d, al + oa, sw128_desc(bh + o, 2048), idesc, 1u);
                     }
                 }
-                mma_commit(&S.tma_empty[s]);
-                mma_commit(&S.a_empty[sa]);
-                if (last) mma_commit(&S.acc_full[j]);
+                mma_commit(&S.kb_done[s]);
+                if (++kc == CHUNK || k == nkb - 1) {
+                    mma_commit(&S.acc_full[j]);
+                    kc = 0;
+                    ++c;
+                }
                 done = k + 1;
             }
             // the last MMAs must finish before tensor memory is released
-            if (done > 0 && !mbar_wait(&S.a_empty[(done - 1) & 1], ((done - 1) >> 1) & 1)) atomicOr(err, 32);
+            if (done > 0 && !mbar_wait(&S.kb_done[(done - 1) % NT], ((done - 1) / NT) & 1)) atomicOr(err, 32);
         }
     } else if (warp >= W_PRO0 && warp < W_PRO0 + N_PRO) {
-        // lane quadrant q of tensor memory = pairs 32 q .. 32 q + 31; half h of each K-block
-        const int q = warp & 3, h = (warp - W_PRO0) >> 2;
+        // lane quadrant q of tensor memory = pairs 32 q .. 32 q + 31; quarter t of
+        // each K-block (16 points: 16-byte chunks 4 (t & 1) .. + 3 of F0 half t >> 1)
+        const int q = warp & 3, t = (warp - W_PRO0) >> 2, h = t >> 1, j0 = 4 * (t & 1);
         const int i = 32 * q + lane;
         const int2 bc = S.pf[i];
-        const bool live = bc.x >= 0;
-        const int rb = live ? bc.x : 0, rc = live ? bc.y : 0;
-        // row r, 16-byte chunk j of a 128-byte-swizzled F0 half lives at r*128 + ((j ^ (r & 7)) << 4)
-        const int ob = rb * 128, sb = rb & 7, oc = rc * 128, sc = rc & 7;
-        const uint32_t lanebase = ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h);
+        const bool pair = bc.x >= 0;
+        const int rb = pair ? bc.x : 0, rc = pair ? bc.y : 0;
+        // F0 row r (relative to the tile's first shell, absolute K-block row g = f0_row0 +
+        // shell_lo + r): 16-byte chunk j of half h at r*256 + 128 h + ((j ^ (g & 7)) << 4)
+        const int g0 = f0_row0 + w.shell_lo;
+        const int ob = rb * 256 + 128 * h, sb = (g0 + rb) & 7, oc = rc * 256 + 128 * h, sc = (g0 + rc) & 7;
+        const uint32_t lanebase = ((uint32_t)(32 * q) << 16) + (uint32_t)(8 * t);
         for (int k = 0; k < nkb && !S.abort; ++k) {
-            const int s = k % NT, u = k / NT, sa = k & 1, ua = k >> 1;
-            if (!mbar_wait(&S.tma_full[s], u & 1) || (ua > 0 && !mbar_wait(&S.a_empty[sa], (ua - 1) & 1))) {
+            const int s = k % NT, u = k / NT, sa = k & 1;
+            if (!mbar_wait(&S.tma_full[s], u & 1) ||
+                (k >= 2 && !mbar_wait(&S.kb_done[(k - 2) % NT], ((k - 2) / NT) & 1))) {
                 set_abort(S, err, 8);
                 break;
             }
             tc_fence_after();
-            const uint8_t* f0 = reinterpret_cast<const uint8_t*>(S.f0[s][h]);
-            uint32_t vh[16], vl[16];
+            const bool live = pair && (long long)(k / unit.len) * lsup + unit.start + k % unit.len < nkb_real;
+            const uint8_t* f0 = S.f0[s];
+            uint32_t vh[8], vl[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = j0 + jj;
                 uint64_t p01 = 0, p23 = 0;
                 if (live) {
                     const float4 fb = *reinterpret_cast<const float4*>(f0 + ob + ((j ^ sb) << 4));
@@ -424,19 +440,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 float p0, p1, p2, p3, h0, h1, h2, h3;
                 unpack64(p01, p0, p1);
                 unpack64(p23, p2, p3);
-                vh[2 * j] = pack2<F16>(p0, p1);
-                vh[2 * j + 1] = pack2<F16>(p2, p3);
-                unpack2<F16>(vh[2 * j], h0, h1);
-                unpack2<F16>(vh[2 * j + 1], h2, h3);
+                vh[2 * jj] = pack2<F16>(p0, p1);
+                vh[2 * jj + 1] = pack2<F16>(p2, p3);
+                unpack2<F16>(vh[2 * jj], h0, h1);
+                unpack2<F16>(vh[2 * jj + 1], h2, h3);
                 float r0, r1, r2, r3;
                 unpack64(fsub2(p01, pack64(h0, h1)), r0, r1);
                 unpack64(fsub2(p23, pack64(h2, h3)), r2, r3);
-                vl[2 * j] = pack2<F16>(r0, r1);
-                vl[2 * j + 1] = pack2<F16>(r2, r3);
+                vl[2 * jj] = pack2<F16>(r0, r1);
+                vl[2 * jj + 1] = pack2<F16>(r2, r3);
             }
             const uint32_t ta = tmem + lanebase + COL_A + (uint32_t)sa * 64;
-            tmem_st16(ta, vh);
-            if (nprod == 3) tmem_st16(ta + 32, vl);
+            tmem_st8(ta, vh);
+            if (nprod == 3) tmem_st8(ta + 32, vl);
             tmem_st_wait();
             tc_fence_before();
             __syncwarp();
@@ -496,8 +512,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
-cudaError_t launch_contract_tc(bool f16, const TcMaps& maps, int f0_rows, int f0_row0, int plane_rows,
-                               const TcWork* works, const TcUnit* units, int nunits,
+cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_row0, const uint32_t* planes,
+                               int groups, long long nkb, const TcWork* works, const TcUnit* units, int nunits,
                                int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
                                unsigned* pace, cudaStream_t st) {
@@ -534,7 +550,7 @@ cudaError_t launch_contract_tc(bool f16, const TcMaps& maps, int f0_rows, int f0
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     unsigned* pc = paced ? pace : nullptr;
-    return cudaLaunchKernelEx(&cfg, kern, maps, f0_rows, f0_row0, plane_rows, works, pair_shells, pair_base, fmax2, bound_mul, units, lsup, nsup,
+    return cudaLaunchKernelEx(&cfg, kern, f0, f0_rows, f0_row0, planes, groups, nkb, works, pair_shells, pair_base, fmax2, bound_mul, units, lsup, nsup,
                               nprod, chunk_kb, partial, err, pc, drift);
 }
 
