@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--shells", type=int, default=64)
     ap.add_argument("--width", type=float, default=2.0, help="shell width in k_f")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "split_bf16", "split_f16", "bf16"])
+    ap.add_argument("--prec", default="split_f16", choices=["fp32", "split_bf16", "split_f16", "bf16"])
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip timing the plain FP32 CUDA-core contraction beside the split path")
     ap.add_argument("--chunk", type=int, default=0, help="tensor-core FP32 accumulation chunk (points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -315,6 +317,32 @@ def main():
                        "counts_s": round(t_counts, 3)},
             "phases_ms": {"filter_fft": fft_ms, "contraction": con_ms, "reduce": red_ms},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": ck}
+    # the plain FP32 CUDA-core path on the same input (shared counts and workspace),
+    # for the split-vs-FP32 speedup and the largest departure between the two
+    if args.prec != "fp32" and not args.no_fp32_compare:
+        ref = bsp.Bispectrum(args.n, BOX, edges, (0, 2, 4), prec="fp32", counts_from=est, ws=est.ws)
+        ref.compute(d)
+        torch.cuda.synchronize()
+        bsp.bsp_set_profiling(ref.plan, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k32 = 2
+        e0.record(stream)
+        for _ in range(k32):
+            ref.compute(d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / k32
+        ph32, nc32, _ = bsp.bsp_phase_times(ref.plan)
+        bsp.bsp_set_profiling(ref.plan, False)
+        ph32 = [p / max(nc32, 1) for p in ph32]
+        Bs = est.compute(d).clone()
+        Bf = ref.compute(d)
+        rms = torch.sqrt(torch.mean(Bf * Bf, dim=1, keepdim=True))
+        dev = torch.max(torch.abs(Bs - Bf) / torch.maximum(torch.abs(Bf), rms)).item()
+        line["fp32_compare"] = {"ms_per_step": ms32, "contraction_ms": ph32[1], "filter_fft_ms": ph32[0],
+                                "speedup_step": ms32 / ms, "speedup_contraction": ph32[1] / con_ms,
+                                "max_rel_dev_vs_fp32": dev, "steps": k32}
+        ref.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         info = cpu_sample(dk, args.n, edges)
         step_s = info["t_full"] + 3 * args.shells * info["t_field"] + outputs * info["t_bin"]

@@ -248,7 +248,7 @@ TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, i
         ahi[p] = std::max(ahi[p], t[0]);
     }
     // per pair: (tile first work, tile a_lo, boxes per slot, pair index within tile)
-    struct TileRef { int work0, alo, nbs, p0; };
+    struct TileRef { int work0, alo, nbs, p0, per; };
     std::vector<TileRef> ref(pl.size());
     size_t i = 0;
     while (i < pl.size()) {
@@ -266,19 +266,21 @@ TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, i
         std::vector<int> boxes;
         for (int si : out_slots)
             for (int b = 0; b < nbs; ++b) boxes.push_back(si * pad + lo + 8 * b);
+        // works of at most 12 boxes (N <= 96), split evenly
         const int work0 = (int)h.works.size();
-        for (size_t b0 = 0; b0 < boxes.size(); b0 += 16) {
+        const int nwk = ((int)boxes.size() + 11) / 12, per = ((int)boxes.size() + nwk - 1) / nwk;
+        for (size_t b0 = 0; b0 < boxes.size(); b0 += per) {
             TcWork w{};
             w.pair0 = (int)i;
             w.npairs = (int)(j - i);
             w.shell_lo = slo;
             w.nshell = shi - slo + 1;
-            w.nbox = (int)std::min<size_t>(16, boxes.size() - b0);
+            w.nbox = (int)std::min<size_t>(per, boxes.size() - b0);
             w.n = (8 * w.nbox + 15) / 16 * 16;
             for (int b = 0; b < w.nbox; ++b) w.box_field[b] = boxes[b0 + b];
             h.works.push_back(w);
         }
-        for (size_t p = i; p < j; ++p) ref[p] = TileRef{work0, lo, nbs, (int)i};
+        for (size_t p = i; p < j; ++p) ref[p] = TileRef{work0, lo, nbs, (int)i, per};
         i = j;
     }
     for (auto& p : pl) h.pairs.push_back(int2{p.first, p.second});
@@ -288,7 +290,9 @@ TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, i
             const int p = pidx[{bins[b][1], bins[b][2]}];
             const TileRef& t = ref[p];
             const int box = (int)si * t.nbs + (bins[b][0] - t.alo) / 8;
-            h.loc[si * bins.size() + b] = BinLoc{t.work0 + box / 16, p - t.p0, 8 * (box % 16) + (bins[b][0] - t.alo) % 8, 0};
+            // tensor-core slots are [field column][pair]: "row" holds the column
+            h.loc[si * bins.size() + b] = BinLoc{t.work0 + box / t.per, 8 * (box % t.per) + (bins[b][0] - t.alo) % 8,
+                                                 p - t.p0, 0};
         }
     assign_units(h, npts, nsm);
     return h;
@@ -952,6 +956,7 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
         if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
         double* partial = (double*)(base + L.partial);
         double* tout = (double*)(base + L.tout);
+        CK(cudaMemsetAsync(partial, 0, p->tc_sched.units.size() * TC_UNIT * sizeof(double), st));
         cudaError_t e = launch_contract_tc(f16 != 0, f0, p->kb_rows32, 0, hi, p->groups16, (long long)p->nkb(),
                                            p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
@@ -1096,6 +1101,8 @@ bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* s
         if ((ms = mark(p, st, 1)) != BSP_OK) return ms;
         double* part = (double*)(base + L.partial);
         double* upart = (double*)(base + L.partial + p->tc_part_bytes);
+        CK(cudaMemsetAsync(part, 0, p->tc_sched.units.size() * TC_UNIT * sizeof(double), st));
+        if (p->need_u) CK(cudaMemsetAsync(upart, 0, p->tc_u_sched.units.size() * TC_UNIT * sizeof(double), st));
         cudaError_t e = launch_contract_tc(f16 != 0, f0, p->kb_rows32, 0, hi, p->groups16, (long long)p->nkb(),
                                            p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,

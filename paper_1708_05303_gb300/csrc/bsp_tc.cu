@@ -4,7 +4,7 @@
 //   T^l[a; b, c] = sum_x F^l_a(x) F^0_b(x) F^0_c(x),
 // is a dense contraction over x once the pair products P_bc = F^0_b F^0_c
 // are formed: D[pair][row] = sum_x P_pair(x) F_row(x), rows = fields (l, a).
-// A CTA owns one tile -- 128 pairs (the MMA M) times N <= 128 field rows --
+// A CTA owns one tile -- 128 pairs (the MMA M) times N <= 96 field rows --
 // and one x-segment, and runs a warp-specialised pipeline per K-block of 64
 // points:
 //   warp 0      bulk copies (TMA engine, no tensor map): the F^0 rows (FP32)
@@ -16,13 +16,14 @@
 //               both in tensor memory, where the MMA reads its A operand;
 //   warp 1      one thread issues tcgen05.mma kind::f16, M=128, K=16, A from
 //               tensor memory, B (field planes) from shared memory:
-//               D += P_hi F_hi + P_hi F_lo + P_lo F_hi (split products;
-//               one product for the plain 16-bit mode), FP32 accumulators
-//               in tensor memory;
-//   warps 20-23 drain the accumulator every `chunk` K-blocks (tcgen05.ld),
-//               add it to a running FP32 sum in tensor memory, and every
-//               FLUSH_KB K-blocks add that sum, unscaled, to the CTA's FP64
-//               slot in global memory.
+//               D += P_hi F_hi and, in a separate accumulator, E += P_hi F_lo
+//               + P_lo F_hi (split products; D alone for the plain 16-bit
+//               mode), FP32 accumulators in tensor memory;
+//   warps 20-23 drain D every `chunk` K-blocks and E every CORR_KB K-blocks
+//               (tcgen05.ld), add them to a running FP32 sum in tensor
+//               memory, and every FLUSH_KB K-blocks add that sum, unscaled,
+//               to the CTA's FP64 slot in global memory (fire-and-forget
+//               reductions).
 // Two accumulator buffers and two A buffers in tensor memory keep TMA, the
 // CUDA-core prologue, the MMAs and the epilogue overlapped.  Every mbarrier
 // wait is bounded; on timeout the CTA records an error code, stops, waits
@@ -35,15 +36,21 @@ namespace bsp {
 namespace {
 
 constexpr int TC_M = 128;        // pairs per tile = MMA M
-constexpr int TC_NMAX = 128;     // field rows per tile = MMA N (max)
+constexpr int TC_NMAX = 96;      // field rows per tile = MMA N (max)
+constexpr int TC_SLOT = 128 * 128;   // FP64 values per CTA slot of the partial sums, [column][pair]
 constexpr int TC_KB = 64;        // x-points per K-block (128 bytes of 16-bit values)
 constexpr int NT = 4;            // TMA ring stages (F0 rows + field planes)
 constexpr int TC_MAXSH = 64;     // F0 rows per tile
 constexpr int TC_THREADS = 768;  // 24 warps
 constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, N_PRO = 16, W_EPI0 = 20;
-// tensor memory columns: acc0 [0,128) acc1 [128,256) running sum [256,384)
-// A buffers [384,448) and [448,512): hi in the first 32 columns, lo in the next 32
-constexpr uint32_t TMEM_COLS = 512, COL_SUM = 256, COL_A = 384;
+// tensor memory columns: the P_hi F_hi accumulators D0 [0,96) and D1 [96,192),
+// drained every chunk; the correction accumulator E = P_hi F_lo + P_lo F_hi
+// [192,288), drained every CORR_KB K-blocks; the running sum [288,384); the A
+// buffers [384,448) and [448,512), hi in the first 32 columns, lo in the next 32.
+// E's terms are ~2^-11 of D's: kept apart, the tensor core's truncating FP32
+// accumulation no longer loses half an ulp of D on each correction product.
+constexpr uint32_t TMEM_COLS = 512, COL_ACC = 96, COL_CORR = 192, COL_SUM = 288, COL_A = 384;
+constexpr int CORR_KB = 16;      // K-blocks per drain of E (a multiple of the chunk)
 constexpr int FLUSH_KB = 128;    // K-blocks between FP64 flushes of the running sum
 constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
 
@@ -52,7 +59,8 @@ struct TcSmem {
     uint8_t b[NT][TC_NMAX / 8 * 2048];     // [stage][group of 8 fields][hi 1024 B | lo 1024 B]
     // tma_full: a stage's copies landed; kb_done: the MMAs of K-block k finished
     // (frees TMA stage k % NT and A buffer k % 2); a_full: A buffer written
-    uint64_t tma_full[NT], kb_done[NT], a_full[2], acc_full[2], acc_empty[2];
+    // corr_empty: E was read
+    uint64_t tma_full[NT], kb_done[NT], a_full[2], acc_full[2], acc_empty[2], corr_empty;
     uint32_t tmem_base;
     volatile int abort;
     int npc;                  // plane copies per K-block
@@ -259,6 +267,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nkb = nsup * unit.len;
     const int nch = (nkb + CHUNK - 1) / CHUNK;
     const int FL = max(1, FLUSH_KB / CHUNK);   // chunks per FP64 flush
+    const int CC = max(1, CORR_KB / CHUNK);    // chunks per drain of E
     const uint32_t N = (uint32_t)w.n;
 
     if (tid == 0) {
@@ -271,6 +280,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&S.acc_full[j], 1);
             mbar_init(&S.acc_empty[j], 4);
         }
+        mbar_init(&S.corr_empty, 4);
         S.abort = 0;
         // field-plane copies: one per run of consecutive groups
         int npc = 0;
@@ -370,7 +380,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int k = 0; k < nkb; ++k) {
                 const int s = k % NT, u = k / NT, sa = k & 1;
                 const int j = c & 1;
+                const bool efirst = kc == 0 && c % CC == 0;   // first K-block of a drain period of E
                 if (kc == 0 && c >= 2 && !mbar_wait(&S.acc_empty[j], ((c >> 1) - 1) & 1)) {
+                    set_abort(S, err, 2);
+                    break;
+                }
+                if (nprod == 3 && efirst && c > 0 && !mbar_wait(&S.corr_empty, ((c / CC) - 1) & 1)) {
                     set_abort(S, err, 2);
                     break;
                 }
@@ -380,7 +395,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (S.abort) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(j * 128);
+                const uint32_t d = tmem + (uint32_t)j * COL_ACC, de = tmem + COL_CORR;
                 const uint32_t ah = tmem + COL_A + (uint32_t)sa * 64, al = ah + 32;
                 const uint32_t bh = b0 + (uint32_t)s * (uint32_t)sizeof(S.b[0]), bl = bh + 1024;
 #pragma unroll
@@ -388,8 +403,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t o = (uint32_t)kk * 32, oa = (uint32_t)kk * 8;
                     mma_ts(d, ah + oa, sw128_desc(bh + o, 2048), idesc, (kc == 0 && kk == 0) ? 0u : 1u);
                     if (nprod == 3) {
-                        mma_ts(d, ah + oa, sw128_desc(bl + o, 2048), idesc, 1u);
-                        mma_ts(d, al + oa, sw128_desc(bh + o, 2048), idesc, 1u);
+                        mma_ts(de, ah + oa, sw128_desc(bl + o, 2048), idesc, (efirst && kk == 0) ? 0u : 1u);
+                        mma_ts(de, al + oa, sw128_desc(bh + o, 2048), idesc, 1u);
                     }
                 }
                 mma_commit(&S.kb_done[s]);
@@ -462,22 +477,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int q = warp & 3;
         const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
         const int row = 32 * q + lane;
-        double* dst = partial + (size_t)blockIdx.x * (TC_M * TC_NMAX) + (size_t)row * TC_NMAX;
+        // the CTA's FP64 slot, [column][pair] (zeroed before the launch): the flushes are
+        // fire-and-forget reductions, coalesced over the warp's 32 pairs
+        double* dst = partial + (size_t)blockIdx.x * TC_SLOT + row;
         const double rs = 1.0 / (double)S.pscale[row];   // exact: powers of two
         for (int c = 0; c < nch && !S.abort; ++c) {
             const int j = c & 1, g = c % FL;
-            const bool flush = g == FL - 1 || c == nch - 1, first_flush = c < FL;
+            const bool flush = g == FL - 1 || c == nch - 1;
             if (!mbar_wait(&S.acc_full[j], (c >> 1) & 1)) {
                 set_abort(S, err, 64);
                 break;
             }
             tc_fence_after();
+            bool have_sum = g > 0;
+            // every CC chunks, and at the end, E joins the running sum first
+            if (nprod == 3 && ((c + 1) % CC == 0 || c == nch - 1)) {
+                for (uint32_t col = 0; col < N; col += 16) {
+                    uint32_t a[16], m[16];
+                    tmem_ld16(lanebase + COL_CORR + col, a);
+                    if (have_sum) tmem_ld16(lanebase + COL_SUM + col, m);
+                    tmem_ld_wait();
+                    if (have_sum) {
+#pragma unroll
+                        for (int t = 0; t < 16; ++t)
+                            a[t] = __float_as_uint(__uint_as_float(m[t]) + __uint_as_float(a[t]));
+                    }
+                    tmem_st16(lanebase + COL_SUM + col, a);
+                }
+                tmem_st_wait();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.corr_empty);
+                have_sum = true;
+            }
             for (uint32_t col = 0; col < N; col += 16) {
                 uint32_t a[16], m[16];
-                tmem_ld16(lanebase + (uint32_t)(j * 128) + col, a);
-                if (g > 0) tmem_ld16(lanebase + COL_SUM + col, m);
+                tmem_ld16(lanebase + (uint32_t)j * COL_ACC + col, a);
+                if (have_sum) tmem_ld16(lanebase + COL_SUM + col, m);
                 tmem_ld_wait();
-                if (g > 0) {
+                if (have_sum) {
 #pragma unroll
                     for (int t = 0; t < 16; ++t) a[t] = __float_as_uint(__uint_as_float(m[t]) + __uint_as_float(a[t]));
                 }
@@ -485,7 +523,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int t = 0; t < 16; ++t) {
                         const double v = (double)__uint_as_float(a[t]) * rs / (double)S.fscale[col + t];
-                        dst[col + t] = first_flush ? v : dst[col + t] + v;
+                        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(dst + (size_t)(col + t) * TC_M), "d"(v)
+                                     : "memory");
                     }
                 } else {
                     tmem_st16(lanebase + COL_SUM + col, a);
@@ -496,8 +535,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.acc_empty[j]);
         }
-        if (nch == 0)
-            for (uint32_t col = 0; col < N; ++col) dst[col] = 0.0;
     }
     tc_fence_before();
     __syncthreads();

@@ -86,3 +86,33 @@ def test_split_bf16_fullsize_reported(results):
     e = gate_T(results, "split_bf16")
     print("split_bf16 512^3 sampled gate error %.3g" % e)
     assert e <= 2e-4
+
+
+def test_split_f16_worst_bins_against_oracle(results, ora):
+    """Over all 76 272 outputs, find where the split path departs most from the
+    FP32 path (low-k bins, where the sum over x cancels most), and check both
+    against the oracle there: the sampled bins above would miss them."""
+    B32, T32 = results["gpu"]["fp32"]
+    Bs, Ts = results["gpu"]["split_f16"]
+    rms = np.sqrt(np.mean(B32 ** 2, axis=1, keepdims=True))
+    dev = np.abs(Bs - B32) / np.maximum(np.abs(B32), rms)
+    worst = []
+    for f in np.argsort(dev.ravel())[::-1]:
+        t = results["bins"][int(f) % dev.shape[1]]
+        if t not in worst:
+            worst.append(t)
+        if len(worst) == 3:
+            break
+    dk, _ = make_field(FieldModel(n=N, box=BOX, sigma_g=0.3), 1708 + 2)
+    r = ora.bispectrum(dk.astype(np.complex128), N, BOX, linear_edges(64), (0, 2, 4), bins=worst)
+    V, n3 = BOX ** 3, float(N) ** 3
+    e32 = es = 0.0
+    for si, t in enumerate(worst):
+        bi = results["bins"].index(t)
+        for li in range(3):
+            scale = max(abs(r["T"][li, si]), rms[li, 0] * V * n3 * results["counts"][bi])
+            e32 = max(e32, abs(T32[li, bi] - r["T"][li, si]) / scale)
+            es = max(es, abs(Ts[li, bi] - r["T"][li, si]) / scale)
+    print("largest split/FP32 departure %.3g at %s; vs oracle there: split %.3g, fp32 %.3g"
+          % (dev.max(), worst[0], es, e32))
+    assert e32 <= 1e-5 and es <= 1e-5
