@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -236,36 +237,48 @@ void assign_units(TcSched& h, size_t npts, int nsm) {
 // every box of 8 fields is one group of the K-block-major 16-bit planes.
 TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, int pad, size_t npts, int nsm) {
     TcSched h;
-    std::map<std::pair<int, int>, int> pidx;
-    for (auto& t : bins) pidx[{t[1], t[2]}] = 0;
-    std::vector<std::pair<int, int>> pl;
-    for (auto& kv : pidx) pl.push_back(kv.first);
-    for (size_t i = 0; i < pl.size(); ++i) pidx[pl[i]] = (int)i;
-    std::vector<int> alo(pl.size(), 1 << 30), ahi(pl.size(), -1);
+    // a-range of each pair (b, c) over the bins, in groups of 8 shells
+    std::map<std::pair<int, int>, std::pair<int, int>> arange;
     for (auto& t : bins) {
-        int p = pidx[{t[1], t[2]}];
-        alo[p] = std::min(alo[p], t[0]);
-        ahi[p] = std::max(ahi[p], t[0]);
+        auto it = arange.find({t[1], t[2]});
+        if (it == arange.end()) arange[{t[1], t[2]}] = {t[0], t[0]};
+        else it->second = {std::min(it->second.first, t[0]), std::max(it->second.second, t[0])};
     }
-    // per pair: (tile first work, tile a_lo, boxes per slot, pair index within tile)
-    struct TileRef { int work0, alo, nbs, p0, per; };
-    std::vector<TileRef> ref(pl.size());
+    // entries: a pair with a group range of at most 4 groups (a pair whose a-range is
+    // longer appears once per piece), sorted by group range so that the 128 entries of
+    // a tile need few groups: most tiles then fit one work of N <= 96 rows
+    struct Entry { int glo, ghi, b, c; };
+    std::vector<Entry> ent;
+    for (auto& kv : arange) {
+        int glo = kv.second.first / 8;
+        const int ghi = kv.second.second / 8;
+        while (ghi - glo + 1 > 4) {
+            ent.push_back(Entry{glo, glo + 3, kv.first.first, kv.first.second});
+            glo += 4;
+        }
+        ent.push_back(Entry{glo, ghi, kv.first.first, kv.first.second});
+    }
+    std::sort(ent.begin(), ent.end(), [](const Entry& x, const Entry& y) {
+        return std::make_tuple(x.glo, x.ghi, x.b, x.c) < std::make_tuple(y.glo, y.ghi, y.b, y.c);
+    });
+    // per entry: (tile first work, tile first group, groups per slot, tile first entry, boxes per work)
+    struct TileRef { int work0, g0, nbs, e0, per; };
+    std::vector<TileRef> ref(ent.size());
     size_t i = 0;
-    while (i < pl.size()) {
-        int slo = pl[i].second, shi = pl[i].first, lo = alo[i], hi = ahi[i];
+    while (i < ent.size()) {
+        int slo = ent[i].c, shi = ent[i].b, glo = ent[i].glo, ghi = ent[i].ghi;
         size_t j = i + 1;
-        while (j < pl.size() && (int)(j - i) < 128) {
-            int nslo = std::min(slo, pl[j].second), nshi = std::max(shi, pl[j].first);
+        while (j < ent.size() && (int)(j - i) < 128) {
+            const int nslo = std::min(slo, ent[j].c), nshi = std::max(shi, ent[j].b);
             if (nshi - nslo + 1 > 64) break;
             slo = nslo; shi = nshi;
-            lo = std::min(lo, alo[j]); hi = std::max(hi, ahi[j]);
+            glo = std::min(glo, ent[j].glo); ghi = std::max(ghi, ent[j].ghi);
             ++j;
         }
-        lo &= ~7;   // boxes start on a group
-        const int na = hi - lo + 1, nbs = (na + 7) / 8;
+        const int nbs = ghi - glo + 1;
         std::vector<int> boxes;
         for (int si : out_slots)
-            for (int b = 0; b < nbs; ++b) boxes.push_back(si * pad + lo + 8 * b);
+            for (int g = 0; g < nbs; ++g) boxes.push_back(si * pad + 8 * (glo + g));
         // works of at most 12 boxes (N <= 96), split evenly
         const int work0 = (int)h.works.size();
         const int nwk = ((int)boxes.size() + 11) / 12, per = ((int)boxes.size() + nwk - 1) / nwk;
@@ -280,20 +293,27 @@ TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, i
             for (int b = 0; b < w.nbox; ++b) w.box_field[b] = boxes[b0 + b];
             h.works.push_back(w);
         }
-        for (size_t p = i; p < j; ++p) ref[p] = TileRef{work0, lo, nbs, (int)i, per};
+        for (size_t e = i; e < j; ++e) ref[e] = TileRef{work0, glo, nbs, (int)i, per};
         i = j;
     }
-    for (auto& p : pl) h.pairs.push_back(int2{p.first, p.second});
+    std::map<std::pair<int, int>, std::vector<int>> entries_of;   // pair -> its entries
+    for (size_t e = 0; e < ent.size(); ++e) {
+        h.pairs.push_back(int2{ent[e].b, ent[e].c});
+        entries_of[{ent[e].b, ent[e].c}].push_back((int)e);
+    }
     h.loc.resize(out_slots.size() * bins.size());
-    for (size_t si = 0; si < out_slots.size(); ++si)
-        for (size_t b = 0; b < bins.size(); ++b) {
-            const int p = pidx[{bins[b][1], bins[b][2]}];
-            const TileRef& t = ref[p];
-            const int box = (int)si * t.nbs + (bins[b][0] - t.alo) / 8;
+    for (size_t b = 0; b < bins.size(); ++b) {
+        const int a = bins[b][0], ga = a / 8;
+        int e = -1;
+        for (int x : entries_of[{bins[b][1], bins[b][2]}])
+            if (ent[x].glo <= ga && ga <= ent[x].ghi) e = x;
+        const TileRef& t = ref[e];
+        for (size_t si = 0; si < out_slots.size(); ++si) {
+            const int box = (int)si * t.nbs + (ga - t.g0);
             // tensor-core slots are [field column][pair]: "row" holds the column
-            h.loc[si * bins.size() + b] = BinLoc{t.work0 + box / t.per, 8 * (box % t.per) + (bins[b][0] - t.alo) % 8,
-                                                 p - t.p0, 0};
+            h.loc[si * bins.size() + b] = BinLoc{t.work0 + box / t.per, 8 * (box % t.per) + a % 8, e - t.e0, 0};
         }
+    }
     assign_units(h, npts, nsm);
     return h;
 }
