@@ -418,6 +418,61 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
     // FP32 pair factors of the tensor-core path are stored pre-scaled (|F s7| < 2^7)
     const R s7 = fmax2 ? (R)pow2_scale(bound, 7) : (R)1;
     float mx = 0.f;
+    if constexpr (sizeof(R) == 4) {
+        if (kbm && (M & 3) == 0) {
+            // K-block-major output, four consecutive pairs of z per thread: one 16-byte
+            // chunk of each 16-bit plane row and two of the FP32 row
+            const int M4 = M >> 2;
+            for (int e = threadIdx.x; e < M4 * P; e += NTHR) {
+                const int m0 = (e % M4) * 4, p = e / M4, y = y0 + p;
+                if (y >= N) continue;
+                const size_t pos = ((size_t)x * N + y) * M + m0;
+                const size_t kb = pos >> 5;
+                const int w = (int)(pos & 31);   // a multiple of 4
+                cx<R> v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = res[sidx<false, P>(p, m0 + i, M)];
+                if (dst) {
+                    cx<R>* row = reinterpret_cast<cx<R>*>(dst) + (kb * (size_t)lay.rows32 + (size_t)fd.out32) * 32;
+                    const int J = w >> 1;   // 16-byte chunks J, J + 1 of the 256-byte FP32 row
+                    const int Ja = (J & 8) | ((J & 7) ^ r32), Jb = ((J + 1) & 8) | (((J + 1) & 7) ^ r32);
+                    *reinterpret_cast<float4*>(row + 2 * Ja) =
+                        make_float4(v[0].re * s7, v[0].im * s7, v[1].re * s7, v[1].im * s7);
+                    *reinterpret_cast<float4*>(row + 2 * Jb) =
+                        make_float4(v[2].re * s7, v[2].im * s7, v[3].re * s7, v[3].im * s7);
+                    if (f0max)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) mx = fmaxf(mx, fmaxf(fabsf(v[i].re), fabsf(v[i].im)));
+                }
+                if (dhi) {
+                    uint32_t h[4], l[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        // two consecutive z values -> 16-bit hi and lo (x0 in the low half)
+                        const float x0 = v[i].re * sc, x1 = v[i].im * sc;
+                        float h0, h1;
+                        if (f16) {
+                            asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h[i]) : "f"(x1), "f"(x0));
+                            unsigned short a = (unsigned short)(h[i] & 0xFFFFu), b = (unsigned short)(h[i] >> 16);
+                            asm("cvt.f32.f16 %0, %1;" : "=f"(h0) : "h"(a));
+                            asm("cvt.f32.f16 %0, %1;" : "=f"(h1) : "h"(b));
+                            asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l[i]) : "f"(x1 - h1), "f"(x0 - h0));
+                        } else {
+                            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h[i]) : "f"(x1), "f"(x0));
+                            h0 = __uint_as_float(h[i] << 16);
+                            h1 = __uint_as_float(h[i] & 0xFFFF0000u);
+                            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l[i]) : "f"(x1 - h1), "f"(x0 - h0));
+                        }
+                    }
+                    const size_t q = kb * (size_t)lay.groups16 * 512 + (size_t)(((w >> 2) ^ r16) << 2);
+                    *reinterpret_cast<uint4*>(dhi + q) = make_uint4(h[0], h[1], h[2], h[3]);
+                    if (dlo) *reinterpret_cast<uint4*>(dlo + q) = make_uint4(l[0], l[1], l[2], l[3]);
+                }
+            }
+            if (f0max && dst) block_max_to(f0max + fd.out32, mx);
+            return;
+        }
+    }
     for (int e = threadIdx.x; e < M * P; e += NTHR) {
         const int m = e % M, p = e / M, y = y0 + p;
         if (y >= N) continue;

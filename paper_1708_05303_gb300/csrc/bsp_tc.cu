@@ -11,7 +11,7 @@
 //               of the tile's shells and the hi/lo planes of its field
 //               groups, stored by the FFT as the swizzled shared-memory image
 //               (one copy per contiguous run), four stages deep;
-//   warps 4-19  form P = F_b F_c in FP32 (one pair per TMEM lane, a quarter
+//   warps 4-11  form P = F_b F_c in FP32 (one pair per TMEM lane, half a
 //               K-block per warp), split it into 16-bit hi + lo and store
 //               both in tensor memory, where the MMA reads its A operand;
 //   warp 1      one thread issues tcgen05.mma kind::f16, M=128, K=16, A from
@@ -19,7 +19,7 @@
 //               D += P_hi F_hi and, in a separate accumulator, E += P_hi F_lo
 //               + P_lo F_hi (split products; D alone for the plain 16-bit
 //               mode), FP32 accumulators in tensor memory;
-//   warps 20-23 drain D every `chunk` K-blocks and E every CORR_KB K-blocks
+//   warps 12-15 drain D every `chunk` K-blocks and E every CORR_KB K-blocks
 //               (tcgen05.ld), add them to a running FP32 sum in tensor
 //               memory, and every FLUSH_KB K-blocks add that sum, unscaled,
 //               to the CTA's FP64 slot in global memory (fire-and-forget
@@ -41,8 +41,15 @@ constexpr int TC_SLOT = 128 * 128;   // FP64 values per CTA slot of the partial 
 constexpr int TC_KB = 64;        // x-points per K-block (128 bytes of 16-bit values)
 constexpr int NT = 4;            // TMA ring stages (F0 rows + field planes)
 constexpr int TC_MAXSH = 64;     // F0 rows per tile
-constexpr int TC_THREADS = 768;  // 24 warps
-constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, N_PRO = 16, W_EPI0 = 20;
+#ifndef TC_PRO_WARPS
+#define TC_PRO_WARPS 8
+#endif
+// warps: 0 copies, 1 MMA, 4 .. 4 + N_PRO - 1 pair products (N_PRO / 4 per TMEM
+// lane quadrant, each a 64 / (N_PRO / 4)-point part of every K-block), then 4 drain warps
+constexpr int N_PRO = TC_PRO_WARPS, PRO_PTS = 64 / (N_PRO / 4), PRO_CH = PRO_PTS / 4;
+constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, W_EPI0 = W_PRO0 + N_PRO;
+constexpr int TC_THREADS = 32 * (W_EPI0 + 4);
+static_assert(N_PRO == 8 || N_PRO == 16, "pair-product warps: 8 or 16");
 // tensor memory columns: the P_hi F_hi accumulators D0 [0,96) and D1 [96,192),
 // drained every chunk; the correction accumulator E = P_hi F_lo + P_lo F_hi
 // [192,288), drained every CORR_KB K-blocks; the running sum [288,384); the A
@@ -419,9 +426,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (done > 0 && !mbar_wait(&S.kb_done[(done - 1) % NT], ((done - 1) / NT) & 1)) atomicOr(err, 32);
         }
     } else if (warp >= W_PRO0 && warp < W_PRO0 + N_PRO) {
-        // lane quadrant q of tensor memory = pairs 32 q .. 32 q + 31; quarter t of
-        // each K-block (16 points: 16-byte chunks 4 (t & 1) .. + 3 of F0 half t >> 1)
-        const int q = warp & 3, t = (warp - W_PRO0) >> 2, h = t >> 1, j0 = 4 * (t & 1);
+        // lane quadrant q of tensor memory = pairs 32 q .. 32 q + 31; part t of each
+        // K-block: points t * PRO_PTS .., 16-byte chunks j0 .. j0 + PRO_CH - 1 of F0 half h
+        const int q = warp & 3, t = (warp - W_PRO0) >> 2, h = (t * PRO_PTS) >> 5, j0 = ((t * PRO_PTS) & 31) >> 2;
         const int i = 32 * q + lane;
         const int2 bc = S.pf[i];
         const bool pair = bc.x >= 0;
@@ -430,7 +437,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // shell_lo + r): 16-byte chunk j of half h at r*256 + 128 h + ((j ^ (g & 7)) << 4)
         const int g0 = f0_row0 + w.shell_lo;
         const int ob = rb * 256 + 128 * h, sb = (g0 + rb) & 7, oc = rc * 256 + 128 * h, sc = (g0 + rc) & 7;
-        const uint32_t lanebase = ((uint32_t)(32 * q) << 16) + (uint32_t)(8 * t);
+        const uint32_t lanebase = ((uint32_t)(32 * q) << 16) + (uint32_t)(t * PRO_PTS / 2);
         for (int k = 0; k < nkb && !S.abort; ++k) {
             const int s = k % NT, u = k / NT, sa = k & 1;
             if (!mbar_wait(&S.tma_full[s], u & 1) ||
@@ -441,9 +448,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const bool live = pair && (long long)(k / unit.len) * lsup + unit.start + k % unit.len < nkb_real;
             const uint8_t* f0 = S.f0[s];
-            uint32_t vh[8], vl[8];
+            uint32_t vh[2 * PRO_CH], vl[2 * PRO_CH];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
+            for (int jj = 0; jj < PRO_CH; ++jj) {
                 const int j = j0 + jj;
                 uint64_t p01 = 0, p23 = 0;
                 if (live) {
@@ -466,8 +473,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 vl[2 * jj + 1] = pack2<F16>(r2, r3);
             }
             const uint32_t ta = tmem + lanebase + COL_A + (uint32_t)sa * 64;
-            tmem_st8(ta, vh);
-            if (nprod == 3) tmem_st8(ta + 32, vl);
+            if constexpr (PRO_CH == 4) {
+                tmem_st8(ta, *reinterpret_cast<const uint32_t(*)[8]>(vh));
+                if (nprod == 3) tmem_st8(ta + 32, *reinterpret_cast<const uint32_t(*)[8]>(vl));
+            } else {
+                tmem_st16(ta, *reinterpret_cast<const uint32_t(*)[16]>(vh));
+                if (nprod == 3) tmem_st16(ta + 32, *reinterpret_cast<const uint32_t(*)[16]>(vl));
+            }
             tmem_st_wait();
             tc_fence_before();
             __syncwarp();
