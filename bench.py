@@ -289,8 +289,10 @@ def main():
                 "issued_frac": (issued / (con_ms / 1e3) / 1e12) / peak}
     elif con_ms >= fft_ms:
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        # DRAM bytes per launch: none captured yet for this version of the kernel
-        traffic = None
+        # DRAM bytes per launch: ncu capture of this kernel at 160^3 with the same bins and
+        # schedule (7.08 GB, profiles/contract_tc_160cube_64shells.md) scaled by the points
+        traffic = (7.08e9 * (args.n / 160.0) ** 3
+                   if (args.shells, args.prec) == (64, "split_f16") else None)
         ach = flop / (con_ms / 1e3) / 1e12
         roof = {"kernel": "k_contract_tc (tcgen05 split-product contraction)", "bound": "tensor",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
