@@ -425,3 +425,58 @@ def test_modal_beta_inverts_gamma(ora):
 def test_covariance_matches_numpy(ora):
     X = np.random.default_rng(2).standard_normal((40, 7)) * 1e3 + 5e6
     assert np.allclose(ora.covariance(X), np.cov(X, rowvar=False), rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Power-spectrum multipoles (Sec. 2, Eq. PowSpecMultipole)
+# ---------------------------------------------------------------------------
+
+def test_power_parseval(ora):
+    """One shell holding every nonzero mode: V N P^0 = sum_n |delta(n)|^2, which
+    Parseval's theorem fixes from the real field, (V^2/n^3)(sum x^2 - (sum x)^2/n^3)."""
+    from paper_1708_05303_gb300.synth import delta_k_from_real
+
+    n, box = 32, 1000.0
+    x = np.random.default_rng(3).standard_normal((n, n, n)) + 0.3
+    r = ora.power_multipoles(delta_k_from_real(x, box), n, box, [1, 3 ** 0.5 * n / 2 + 1])
+    V = box ** 3
+    assert r["Nk"][0] == n ** 3 - 1
+    lhs = r["P"][0, 0] * r["Nk"][0] * V
+    rhs = V * V / n ** 3 * (np.sum(x * x) - np.sum(x) ** 2 / n ** 3)
+    assert abs(lhs - rhs) <= 1e-12 * rhs
+
+
+def test_power_kaiser_multipoles(ora):
+    """Linear field with Kaiser RSD, delta_s = (1 + f mu^2) g: the multipoles
+    over a wide shell, divided by the mean linear power of its modes, approach
+    the continuum Kaiser factors 1 + 2f/3 + f^2/5, 4f/3 + 4f^2/7, 8f^2/35
+    (sample variance of 6 realisations at 64^3)."""
+    from paper_1708_05303_gb300.synth import FieldModel, make_field
+
+    n, box, f = 64, 1000.0, 0.7
+    edges = [12, 28]
+    kk = (2 * np.pi / box) * np.sqrt(ora.n2_grid(n).astype(float))
+    m = ora.shell_masks(n, edges)[0]
+    acc = np.zeros(3)
+    for s in range(6):
+        dk, amp = make_field(FieldModel(n=n, box=box, quad=0.0, f=f), 500 + s, dtype=np.complex128)
+        P = ora.power_multipoles(dk, n, box, edges)["P"][:, 0]
+        acc += P / np.mean(amp * kk[m] ** -1.5)
+    acc /= 6
+    kaiser = np.array([1 + 2 * f / 3 + f * f / 5, 4 * f / 3 + 4 * f * f / 7, 8 * f * f / 35])
+    assert np.all(np.abs(acc - kaiser) <= 0.03), (acc, kaiser)
+
+
+def test_power_white_noise_shot(ora):
+    """White noise of variance s^2 has |delta|^2 / V = s^2 V / n^3 on every mode:
+    with nbar = n^3 / (V s^2) the shot-subtracted multipoles vanish within
+    sample variance, and so does the anisotropic part."""
+    from paper_1708_05303_gb300.synth import delta_k_from_real
+
+    n, box, sig = 64, 1000.0, 0.8
+    x = np.random.default_rng(7).standard_normal((n, n, n)) * sig
+    V = box ** 3
+    nbar = n ** 3 / (V * sig * sig)
+    r = ora.power_multipoles(delta_k_from_real(x, box), n, box, [4, 12, 20, 30], nbar=nbar)
+    assert np.allclose(r["shot"][0], 1 / nbar)
+    assert np.max(np.abs(r["P"])) * nbar <= 0.1
