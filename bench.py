@@ -248,6 +248,23 @@ def main():
         ms = float(t.item())
     value = outputs * world / (ms / 1e3)
 
+    # power-spectrum multipoles on the same shells (Eq. PowSpecMultipole): one pass over the
+    # pruned half spectrum, HBM-bound; algorithmic bytes = the complex64 modes read
+    est.power(d)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    p0.record(stream)
+    for _ in range(reps):
+        est.power(d)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    pw_ms = p0.elapsed_time(p1) / reps
+    Kp = 0
+    while (Kp + 1) ** 2 < edges[-1] ** 2:
+        Kp += 1
+    nKp, nKzp = (min(args.n, 2 * Kp + 1), min(args.n // 2 + 1, Kp + 1))
+    pw_bytes = nKp * nKp * nKzp * 8.0
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -321,7 +338,10 @@ def main():
                              % (dk.nbytes / 1e6, 3 * args.shells * n3 * 4 / 1e9),
                        "counts_s": round(t_counts, 3)},
             "phases_ms": {"filter_fft": fft_ms, "contraction": con_ms, "reduce": red_ms},
-            "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": ck}
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": ck,
+            "power_multipoles": {"ms": pw_ms, "shells_per_s": args.shells * 3 / (pw_ms / 1e3),
+                                 "algorithmic_bytes": pw_bytes, "achieved_gbs": pw_bytes / (pw_ms / 1e3) / 1e9,
+                                 "frac_hbm": pw_bytes / (pw_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}}
     # the plain FP32 CUDA-core path on the same input (shared counts and workspace),
     # for the split-vs-FP32 speedup and the largest departure between the two
     if args.prec != "fp32" and not args.no_fp32_compare:

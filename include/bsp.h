@@ -250,6 +250,26 @@ bsp_status bsp_compute_host(bsp_plan* plan, const void* delta_k_host, double nba
                             void* stream, double* B_host);
 bsp_status bsp_host_staging_size(const bsp_plan* plan, size_t* bytes);
 
+/*
+ * Power-spectrum multipoles on the plan's shells (Sec. 2, Eq.
+ * PowSpecMultipole, plane-parallel with z the line of sight):
+ *   P^l_a = 1/(V N_a) sum_{n in shell a} w_l(mu_n) |delta(n)|^2,
+ * N_a the number of modes of the full grid in the shell (the half spectrum
+ * counts twice for 0 < n_z < n/2; on the n_z = 0, n/2 planes the Hermitian
+ * part is used), w_l = (2l+1) L_l, for the plan's multipoles.  With
+ * nbar > 0 the Poisson expectation (1/nbar) (1/N_a) sum w_l(mu_n) is
+ * subtracted (the paper does not discuss shot noise).
+ *   delta_k: device complex64 [n][n][n/2+1], continuum normalised.
+ *   ws:      the plan's workspace (bsp_workspace_size bytes, 256-byte
+ *            aligned); its first bytes are overwritten.
+ *   P:       device FP64 [n_ell][n_shells] (out).
+ *   Nk:      device FP64 [n_shells] mode counts (out), or NULL.
+ * Asynchronous on `stream`; deterministic.  Standard plans only (EINVAL for
+ * modal plans, NULL pointers or nbar < 0).
+ */
+bsp_status bsp_power_compute(bsp_plan* plan, const void* delta_k, double nbar, void* ws, void* stream, double* P,
+                             double* Nk);
+
 /* Raw sums T^l = sum_x F^l_a F_b F_c of the last bsp_compute (FP64
  * [n_ell][n_bins], device), copied into T (device).  For tests. */
 bsp_status bsp_last_raw(const bsp_plan* plan, void* ws, void* stream, double* T);

@@ -567,7 +567,7 @@ def power_multipoles(delta_half: np.ndarray, n: int, box: float, edges, ells=(0,
     Hermitian spectrum of ``full_from_half``.  With a number density nbar
     the Poisson expectation of |delta|^2 / V, 1/nbar, is subtracted through
     its weighted shell mean: shot^l_a = (1/nbar) (1/N_a) sum_n w_l(mu_n)
-    (the paper is silent on shot noise; same reading as for the bispectrum).
+    (the paper is silent on shot noise: the Poisson expectation, weighted like the signal).
     Returns dict(P, P_raw, shot [n_ell][n_shells], Nk [n_shells])."""
     V = float(box) ** 3
     full = full_from_half(delta_half, n)

@@ -48,6 +48,7 @@ _SIGS = [
     ("bsp_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_compute_host", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_last_raw", ctypes.c_int, [_P, _P, _P, _P]),
+    ("bsp_power_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P, _P]),
     ("bsp_device_status", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("bsp_set_accumulation_chunk", ctypes.c_int, [_P, ctypes.c_int]),
     ("bsp_plan_tune", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
@@ -236,6 +237,11 @@ def bsp_compute_host(plan: int, delta_k_host: np.ndarray, B_host: np.ndarray, ws
            "bsp_compute_host")
 
 
+def bsp_power_compute(plan: int, delta_k, P, ws, nbar: float = 0.0, stream=None, Nk=None):
+    _check(load().bsp_power_compute(plan, _dptr(delta_k), float(nbar), _dptr(ws), _stream_handle(stream), _dptr(P),
+                                    _dptr(Nk) if Nk is not None else None), "bsp_power_compute")
+
+
 def bsp_last_raw(plan: int, ws, T, stream=None):
     _check(load().bsp_last_raw(plan, _dptr(ws), _stream_handle(stream), _dptr(T)), "bsp_last_raw")
 
@@ -396,6 +402,7 @@ class Bispectrum:
         import torch
 
         self.n, self.box, self.ells = int(n), float(box), tuple(ells)
+        self.edges = [float(e) for e in edges]
         self.plan = bsp_plan_create(n, box, edges, ells, PRECISIONS.get(prec, prec),
                                     BSP_SHOT_NOISE if shot_noise else 0)
         nbytes = bsp_workspace_size(self.plan)
@@ -419,6 +426,17 @@ class Bispectrum:
     def compute_host(self, delta_k_host, B_host, nbar: float = 0.0, stream=None):
         bsp_compute_host(self.plan, delta_k_host, B_host, self.ws, nbar, stream)
         return B_host
+
+    def power(self, delta_k, nbar: float = 0.0, stream=None):
+        """Power-spectrum multipoles P [n_ell][n_shells] and mode counts Nk
+        [n_shells] (FP64, device) of delta_k on the plan's shells; uses the
+        start of the plan's workspace."""
+        import torch
+
+        P = torch.empty((len(self.ells), len(self.edges) - 1), dtype=torch.float64, device="cuda")
+        Nk = torch.empty(len(self.edges) - 1, dtype=torch.float64, device="cuda")
+        bsp_power_compute(self.plan, delta_k, P, self.ws, nbar, stream, Nk)
+        return P, Nk
 
     def raw(self, stream=None):
         import torch

@@ -1250,6 +1250,26 @@ bsp_status bsp_phase_times(bsp_plan* p, double* ms, int* ncalls, int* launches) 
     return BSP_OK;
 }
 
+bsp_status bsp_power_compute(bsp_plan* p, const void* delta_k, double nbar, void* ws, void* stream, double* P,
+                             double* Nk) {
+    if (!p || !delta_k || !ws || !P || !aligned256(ws) || !(nbar >= 0.0)) return BSP_EINVAL;
+    if (p->modal || p->nsh <= 0 || p->ells.size() > 3) return BSP_EINVAL;
+    PowerEll pe{};
+    pe.n = (int)p->ells.size();
+    for (int i = 0; i < pe.n; ++i) pe.ell[i] = p->ells[i];
+    // one FP64 slot per CTA at the start of the workspace (it fits: the
+    // workspace holds at least one field per shell)
+    const long long rows = (long long)p->geom.nK * p->geom.nK;
+    int nblocks = (int)std::min<long long>(rows, 4LL * p->nsm);
+    while (nblocks > 1 && power_partial_bytes(nblocks, p->nsh, pe.n) > p->ws_bytes) nblocks /= 2;
+    if (power_partial_bytes(nblocks, p->nsh, pe.n) > p->ws_bytes) return BSP_ENOMEM;
+    const double V = p->box * p->box * p->box;
+    cudaError_t e = launch_power((const cx<float>*)delta_k, p->geom, p->d_shell_of, p->nsh, pe, V, nbar, nblocks,
+                                 (double*)ws, P, Nk, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "power multipoles");
+    return BSP_OK;
+}
+
 bsp_status bsp_last_raw(const bsp_plan* p, void* ws, void* stream, double* T) {
     if (!p || !ws || !T || !aligned256(ws)) return BSP_EINVAL;
     if (!p->have_counts) return BSP_ESTATE;

@@ -140,6 +140,16 @@ cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_ro
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
                                unsigned* pace, cudaStream_t st);
 
+// ---- launchers (bsp_power.cu) ----
+struct PowerEll {   // the multipoles of a power-spectrum call (even l in {0, 2, 4})
+    int n;
+    int ell[3];
+};
+size_t power_partial_bytes(int nblocks, int nsh, int nell);
+cudaError_t launch_power(const cx<float>* delta, const FftGeom& g, const int16_t* shell_of, int nsh,
+                         const PowerEll& ells, double V, double nbar, int nblocks, double* partial, double* P,
+                         double* Nk, cudaStream_t st);
+
 // ---- launchers (bsp_modal.cu) ----
 cudaError_t launch_modal_assemble(const double* T, const double* U, const int* ells, int n_ell, int nf,
                                   long long nall, int ntrip, double scale, double* S, cudaStream_t st);

@@ -1,0 +1,156 @@
+// bsp_power.cu -- power-spectrum multipoles P^(l)(k) on the shells of a plan.
+//
+// Eq. PowSpecMultipole (Sec. 2): with the line of sight along z (plane-
+// parallel), delta^(l)(k) delta^(0)(-k) = w_l(mu) |delta(k)|^2, and the
+// average over the directions of shell a is the mean over its modes:
+//   P^l_a = 1/(V N_a) sum_{n in a} w_l(mu_n) |delta(n)|^2,   w_l = (2l+1) L_l.
+// The half spectrum holds each mode pair once for 0 < n_z < n/2 (weight 2)
+// and both members on the n_z = 0 and n/2 planes (weight 1 each, with the
+// Hermitian part (delta(n) + conj delta(-n))/2, as the real inverse FFT sees
+// it).  Only |f| <= K per axis can lie in a shell, so only that box is read.
+// One pass: the products w_l |delta|^2 are formed in FP32 (the input is
+// FP32; GB300's FP64 rate is a small fraction of its FP32 rate), summed in
+// FP64 per warp and shell, per CTA, then over CTAs in a fixed order by a
+// second kernel (deterministic), which normalises.
+#include "bsp_internal.h"
+
+namespace bsp {
+
+namespace {
+
+__device__ __forceinline__ float legendre_w(int ell, float mu2) {
+    if (ell == 0) return 1.f;
+    if (ell == 2) return 2.5f * (3.f * mu2 - 1.f);                             // 5 L_2
+    return 1.125f * ((35.f * mu2 - 30.f) * mu2 + 3.f);                         // 9 L_4
+}
+
+constexpr int PW_WARPS = 8;   // warps per CTA
+
+__global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>* __restrict__ delta, FftGeom g,
+                                                                 const int16_t* __restrict__ shell_of, int nsh,
+                                                                 PowerEll ells, double* __restrict__ partial) {
+    // per warp [2 nell + 1][nsh] FP64: sum w|d|^2 per l, sum w per l, mode count
+    extern __shared__ double acc[];
+    const int nell = ells.n, per = (2 * nell + 1) * nsh;
+    for (int i = threadIdx.x; i < PW_WARPS * per; i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    const int N = g.n, H = N / 2 + 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* mine = acc + (size_t)wid * per;
+    const long long rows = (long long)g.nK * g.nK;
+    // one warp per row, 32 consecutive n_z at a time: along a row |n| grows with
+    // n_z, so the lanes of one shell are a contiguous run; a segmented sum over
+    // the run (FP32, at most 32 terms) leaves its total in the run's last lane,
+    // the only writer of that shell in this warp (FP64): no atomics, and every
+    // sum is taken in a fixed order
+    for (long long r = (long long)blockIdx.x * PW_WARPS + wid; r < rows; r += (long long)gridDim.x * PW_WARPS) {
+        const int cx_ = (int)(r / g.nK), cy = (int)(r % g.nK);
+        const int fx = g.pruned ? cx_ - g.K : (cx_ < N / 2 ? cx_ : cx_ - N);
+        const int fy = g.pruned ? cy - g.K : (cy < N / 2 ? cy : cy - N);
+        const int ix = (fx + N) % N, iy = (fy + N) % N;
+        const cx<float>* row = delta + ((size_t)ix * N + iy) * H;
+        const cx<float>* mrow = delta + ((size_t)((N - ix) % N) * N + (N - iy) % N) * H;
+        for (int k0 = 0; k0 < g.nKz; k0 += 32) {
+            const int kz = k0 + lane;
+            int s = -1;
+            float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (kz < g.nKz) {
+                const int fz = kz == N / 2 ? -(N / 2) : kz;
+                const int n2 = fx * fx + fy * fy + fz * fz;
+                if (n2 > 0 && n2 <= g.n2max) s = shell_of[n2];
+                if (s >= 0) {
+                    const cx<float> d = row[kz];
+                    float re = d.re, im = d.im, h = 2.f;
+                    if (kz == 0 || kz == N / 2) {
+                        const cx<float> m = mrow[kz];
+                        re = 0.5f * (re + m.re);
+                        im = 0.5f * (im - m.im);
+                        h = 1.f;
+                    }
+                    const float p = h * (re * re + im * im), mu2 = (float)(fz * fz) / (float)n2;
+                    for (int l = 0; l < nell; ++l) {
+                        const float w = legendre_w(ells.ell[l], mu2);
+                        v[l] = w * p;
+                        v[3 + l] = w * h;
+                    }
+                    v[6] = h;
+                }
+            }
+            if (__all_sync(0xffffffffu, s < 0)) continue;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int so = __shfl_up_sync(0xffffffffu, s, o);
+                const bool take = lane >= o && so == s;
+#pragma unroll
+                for (int t = 0; t < 7; ++t) {
+                    const float x = __shfl_up_sync(0xffffffffu, v[t], o);
+                    if (take) v[t] += x;
+                }
+            }
+            const int snext = __shfl_down_sync(0xffffffffu, s, 1);
+            if (s >= 0 && (lane == 31 || snext != s)) {
+                for (int l = 0; l < nell; ++l) {
+                    mine[l * nsh + s] += (double)v[l];
+                    mine[(nell + l) * nsh + s] += (double)v[3 + l];
+                }
+                mine[2 * nell * nsh + s] += (double)v[6];
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    double* dst = partial + (size_t)blockIdx.x * per;
+    for (int i = threadIdx.x; i < per; i += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < PW_WARPS; ++w) t += acc[(size_t)w * per + i];   // fixed order
+        dst[i] = t;
+    }
+}
+
+__global__ void k_power_final(const double* __restrict__ partial, int nblocks, int nsh, int nell, double V,
+                              double nbar, double* __restrict__ P, double* __restrict__ Nk) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nell * nsh) return;
+    const int l = t / nsh, s = t % nsh, per = (2 * nell + 1) * nsh;
+    double sp = 0.0, sw = 0.0, sn = 0.0;
+    for (int b = 0; b < nblocks; ++b) {   // fixed order: deterministic
+        const double* q = partial + (size_t)b * per;
+        sp += q[l * nsh + s];
+        sw += q[(nell + l) * nsh + s];
+        sn += q[2 * nell * nsh + s];
+    }
+    double v = 0.0;
+    if (sn > 0.0) {
+        v = sp / (V * sn);
+        if (nbar > 0.0) v -= sw / (nbar * sn);
+    }
+    P[t] = v;
+    if (Nk && l == 0) Nk[s] = sn;
+}
+
+}  // namespace
+
+size_t power_partial_bytes(int nblocks, int nsh, int nell) {
+    return (size_t)nblocks * (size_t)(2 * nell + 1) * (size_t)nsh * sizeof(double);
+}
+
+cudaError_t launch_power(const cx<float>* delta, const FftGeom& g, const int16_t* shell_of, int nsh,
+                         const PowerEll& ells, double V, double nbar, int nblocks, double* partial, double* P,
+                         double* Nk, cudaStream_t st) {
+    const size_t smem = (size_t)PW_WARPS * (2 * ells.n + 1) * nsh * sizeof(double);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    static size_t set = 0;   // raised once per size, never inside a graph capture
+    cudaError_t e;
+    if (smem > 48 * 1024 && smem > set) {
+        if ((e = cudaFuncSetAttribute(k_power_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        set = smem;
+    }
+    k_power_partial<<<nblocks, 32 * PW_WARPS, smem, st>>>(delta, g, shell_of, nsh, ells, partial);
+    const int nt = ells.n * nsh;
+    k_power_final<<<(nt + 127) / 128, 128, 0, st>>>(partial, nblocks, nsh, ells.n, V, nbar, P, Nk);
+    return cudaGetLastError();
+}
+
+}  // namespace bsp
