@@ -102,8 +102,9 @@ def cic_interlaced(model: FieldModel, seed: int, n_particles: int = 4 * 2 ** 20,
     Poisson counts per cell -> positions uniform within the cell -> CIC
     deposit on grid 1 and on grid 2 (particles shifted by -H/2 per axis, H the
     cell size, i.e. grid 2 sampled at +H/2) -> delta_i = count/nbar_cell - 1
-    -> delta(k) = [delta_1(k) + e^{i k.(H/2)(1,1,1)} delta_2(k)]/2 divided by
-    prod_i sinc^2(pi n_i / n).  Returns (half spectrum, realised N_p, nbar)."""
+    -> delta(k) = [delta_1(k) + e^{-i k.(H/2)(1,1,1)} delta_2(k)]/2 divided by
+    prod_i sinc^2(pi n_i / n) (grid 2's cell j stands for position (j + 1/2) H,
+    hence the phase).  Returns (half spectrum, realised N_p, nbar)."""
     n, box = model.n, model.box
     dk, _ = make_field(model, seed, dtype=np.complex128)
     ds = np.fft.irfftn(dk * (n ** 3 / box ** 3), s=(n, n, n), axes=(0, 1, 2))
@@ -139,7 +140,7 @@ def cic_interlaced(model: FieldModel, seed: int, n_particles: int = 4 * 2 ** 20,
     fx = _freqs(n)
     fz = np.arange(n // 2 + 1, dtype=np.float64)
     fz[n // 2] = -(n // 2)
-    phase = np.exp(1j * math.pi / n * (fx[:, None, None] + fx[None, :, None] + fz[None, None, :]))
+    phase = np.exp(-1j * math.pi / n * (fx[:, None, None] + fx[None, :, None] + fz[None, None, :]))
     d = 0.5 * (d1 + phase * d2)
     sx = np.sinc(fx / n)
     sz = np.sinc(fz / n)

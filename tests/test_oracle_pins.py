@@ -480,3 +480,49 @@ def test_power_white_noise_shot(ora):
     r = ora.power_multipoles(delta_k_from_real(x, box), n, box, [4, 12, 20, 30], nbar=nbar)
     assert np.allclose(r["shot"][0], 1 / nbar)
     assert np.max(np.abs(r["P"])) * nbar <= 0.1
+
+
+# ---------------------------------------------------------------------------
+# Density input stage: cloud-in-cell with interlacing
+# ---------------------------------------------------------------------------
+
+def test_density_single_particle_closed_form(ora):
+    """One particle on a grid node x0: grid 1 holds it in one cell, grid 2 (cells
+    at half offsets) in eight with weight 1/8, so after the phase and the window
+    delta(k) = V e^{-ik.x0} [1 + prod_a cos(k_a H/2)] / (2 W(k)) for k != 0."""
+    n, box = 16, 1000.0
+    H = box / n
+    x0 = np.array([3, 5, 7]) * H
+    d, nbar = ora.density_from_particles(x0[None, :], n, box)
+    assert nbar == 1 / box ** 3
+    f = ora.freq_axis(n).astype(float)
+    fz = np.arange(n // 2 + 1, dtype=float)
+    fz[n // 2] = -(n // 2)
+    kx, ky, kz = [2 * np.pi / box * a for a in np.meshgrid(f, f, fz, indexing="ij")]
+    W = (np.sinc(kx * H / (2 * np.pi)) * np.sinc(ky * H / (2 * np.pi)) * np.sinc(kz * H / (2 * np.pi))) ** 2
+    cf = (0.5 * box ** 3 * np.exp(-1j * (kx * x0[0] + ky * x0[1] + kz * x0[2]))
+          * (1 + np.cos(kx * H / 2) * np.cos(ky * H / 2) * np.cos(kz * H / 2)) / W)
+    cf[0, 0, 0] = 0
+    assert np.max(np.abs(d - cf)) <= 1e-12 * np.max(np.abs(cf))
+
+
+def test_density_lattice_is_uniform(ora):
+    """One particle at each cell centre fills both grids uniformly: delta = 0."""
+    n, box = 16, 1000.0
+    g = (np.arange(n) + 0.5) * (box / n)
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    d, _ = ora.density_from_particles(P, n, box)
+    assert np.max(np.abs(d)) <= 1e-9
+
+
+def test_density_plane_wave_amplitude(ora):
+    """Particles drawn from 1 + A cos(2 pi m x / L): the mode (m, 0, 0) of the
+    interlaced, deconvolved delta(k) is V A / 2 within Poisson noise, and real."""
+    n, box, m, A = 32, 1000.0, 3, 0.5
+    rng = np.random.default_rng(1)
+    x = rng.random(4_000_000) * box
+    x = x[rng.random(x.size) < (1 + A * np.cos(2 * np.pi * m * x / box)) / (1 + A)][:2_000_000]
+    P = np.stack([x, rng.random(x.size) * box, rng.random(x.size) * box], axis=1)
+    d, _ = ora.density_from_particles(P, n, box)
+    want = box ** 3 * A / 2
+    assert abs(d[m, 0, 0] - want) <= 0.01 * want
