@@ -265,6 +265,33 @@ def main():
         Kp += 1
     nKp, nKzp = (min(args.n, 2 * Kp + 1), min(args.n // 2 + 1, Kp + 1))
     pw_bytes = nKp * nKp * nKzp * 8.0
+    # density input stage (CIC + interlacing + forward FFT) on the particle workload's
+    # shape: 256^3 grid, 4 Mi particles (uniform positions: the cost does not depend on them)
+    dn, dnp = 256, 4 * 2 ** 20
+    dpos = torch.rand((dnp, 3), device="cuda", dtype=torch.float32,
+                      generator=torch.Generator(device="cuda").manual_seed(SEED)) * BOX
+    dws = None
+    _, _ = bsp.density_from_particles(dpos, dn, BOX)
+    torch.cuda.synchronize()
+    import ctypes as _ct
+    _nb = _ct.c_size_t()
+    bsp.load().bsp_density_workspace_size(dn, _ct.byref(_nb))
+    dws = torch.empty(_nb.value, dtype=torch.uint8, device="cuda")
+    bsp.density_from_particles(dpos, dn, BOX, ws=dws)
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(5):
+        bsp.density_from_particles(dpos, dn, BOX, ws=dws)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    den_ms = q0.elapsed_time(q1) / 5
+    nh = dn * dn * (dn // 2 + 1)
+    # algorithmic bytes: positions, two grids written (atomics) and read, the two
+    # spectra written by the z pass, read + written by the y and x passes, read by
+    # the combine, and the output written
+    den_bytes = dnp * 12.0 + 2 * dn ** 3 * 4 * 2 + 2 * nh * 8 * 5 + nh * 8
+    del dpos, dws
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -339,6 +366,10 @@ def main():
                        "counts_s": round(t_counts, 3)},
             "phases_ms": {"filter_fft": fft_ms, "contraction": con_ms, "reduce": red_ms},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": ck,
+            "density_stage": {"ms": den_ms, "grid": dn, "particles": dnp,
+                              "particles_per_s": dnp / (den_ms / 1e3), "algorithmic_bytes": den_bytes,
+                              "achieved_gbs": den_bytes / (den_ms / 1e3) / 1e9,
+                              "frac_hbm": den_bytes / (den_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
             "power_multipoles": {"ms": pw_ms, "shells_per_s": args.shells * 3 / (pw_ms / 1e3),
                                  "algorithmic_bytes": pw_bytes, "achieved_gbs": pw_bytes / (pw_ms / 1e3) / 1e9,
                                  "frac_hbm": pw_bytes / (pw_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}}

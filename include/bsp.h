@@ -270,6 +270,27 @@ bsp_status bsp_host_staging_size(const bsp_plan* plan, size_t* bytes);
 bsp_status bsp_power_compute(bsp_plan* plan, const void* delta_k, double nbar, void* ws, void* stream, double* P,
                              double* Nk);
 
+/*
+ * The density input the estimators take, from particles: cloud-in-cell
+ * assignment on two n^3 grids (cells at j H and at (j + 1/2) H, H = box/n),
+ * delta_g = count / (N_p / n^3) - 1, a forward real-to-complex FFT of each,
+ * the interlaced average delta(k) = (V/n^3)[X1 + e^{-ik.(H/2)(1,1,1)} X2]/2
+ * and the CIC window divided out, prod_a sinc^2(pi n_a / n).  The paper
+ * starts from a density grid; this is the standard preparation of one from
+ * a particle catalogue (no counterpart in the paper).
+ *   pos:      device float32 [n_particles][3], positions in [0, box).
+ *   ws:       device workspace of bsp_density_workspace_size(n) bytes,
+ *             256-byte aligned (~16 n^3 bytes); ws_bytes its size.
+ *   delta_k:  device complex64 [n][n][n/2+1] (out), continuum normalised.
+ *   nbar:     host, N_p / V (out), or NULL.
+ * n even, of the form 2^a 3^b 5^c (EINVAL otherwise); asynchronous on
+ * `stream`.  The deposit uses floating-point atomics, so results vary in the
+ * last bits from call to call.
+ */
+bsp_status bsp_density_workspace_size(int n, size_t* bytes);
+bsp_status bsp_density_cic(int n, double box, long long n_particles, const float* pos, void* ws, size_t ws_bytes,
+                           void* stream, void* delta_k, double* nbar);
+
 /* Raw sums T^l = sum_x F^l_a F_b F_c of the last bsp_compute (FP64
  * [n_ell][n_bins], device), copied into T (device).  For tests. */
 bsp_status bsp_last_raw(const bsp_plan* plan, void* ws, void* stream, double* T);

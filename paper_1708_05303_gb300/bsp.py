@@ -49,6 +49,9 @@ _SIGS = [
     ("bsp_compute_host", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_last_raw", ctypes.c_int, [_P, _P, _P, _P]),
     ("bsp_power_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P, _P]),
+    ("bsp_density_workspace_size", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    ("bsp_density_cic", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_longlong, _P, _P, ctypes.c_size_t, _P,
+                                       _P, ctypes.POINTER(ctypes.c_double)]),
     ("bsp_device_status", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("bsp_set_accumulation_chunk", ctypes.c_int, [_P, ctypes.c_int]),
     ("bsp_plan_tune", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
@@ -240,6 +243,25 @@ def bsp_compute_host(plan: int, delta_k_host: np.ndarray, B_host: np.ndarray, ws
 def bsp_power_compute(plan: int, delta_k, P, ws, nbar: float = 0.0, stream=None, Nk=None):
     _check(load().bsp_power_compute(plan, _dptr(delta_k), float(nbar), _dptr(ws), _stream_handle(stream), _dptr(P),
                                     _dptr(Nk) if Nk is not None else None), "bsp_power_compute")
+
+
+def density_from_particles(pos, n: int, box: float, ws=None, stream=None):
+    """delta(k) (complex64 [n][n][n/2+1], device) and nbar from particle
+    positions (float32 [N_p][3] CUDA tensor, box units) by CIC with
+    interlacing (bsp_density_cic).  ``ws`` may be a reusable uint8 CUDA
+    tensor of bsp_density_workspace_size(n) bytes."""
+    import torch
+
+    nb = ctypes.c_size_t()
+    _check(load().bsp_density_workspace_size(int(n), ctypes.byref(nb)), "bsp_density_workspace_size")
+    if ws is None or ws.numel() < nb.value:
+        ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+    out = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
+    nbar = ctypes.c_double()
+    pos = pos.contiguous()
+    _check(load().bsp_density_cic(int(n), float(box), int(pos.shape[0]), _dptr(pos), _dptr(ws), int(ws.numel()),
+                                  _stream_handle(stream), _dptr(out), ctypes.byref(nbar)), "bsp_density_cic")
+    return out, nbar.value
 
 
 def bsp_last_raw(plan: int, ws, T, stream=None):

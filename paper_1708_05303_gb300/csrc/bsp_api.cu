@@ -1270,6 +1270,37 @@ bsp_status bsp_power_compute(bsp_plan* p, const void* delta_k, double nbar, void
     return BSP_OK;
 }
 
+static bool density_geom(int n, FftGeom* g) {
+    if (n < 8 || n % 2 != 0 || n > 2048) return false;
+    *g = FftGeom{};
+    g->n = n;
+    g->K = n / 2;
+    g->nK = n;
+    g->pruned = 0;
+    g->nKz = n / 2 + 1;
+    g->n2max = 3 * (n / 2) * (n / 2);
+    return radix_plan(n, g->rad, &g->nrad) && radix_plan(n / 2, g->rad_h, &g->nrad_h);
+}
+
+bsp_status bsp_density_workspace_size(int n, size_t* bytes) {
+    FftGeom g;
+    if (!bytes || !density_geom(n, &g)) return BSP_EINVAL;
+    *bytes = density_layout(n).end;
+    return BSP_OK;
+}
+
+bsp_status bsp_density_cic(int n, double box, long long n_particles, const float* pos, void* ws, size_t ws_bytes,
+                           void* stream, void* delta_k, double* nbar) {
+    FftGeom g;
+    if (!density_geom(n, &g) || !(box > 0.0) || n_particles <= 0 || !pos || !ws || !delta_k || !aligned256(ws))
+        return BSP_EINVAL;
+    if (ws_bytes < density_layout(n).end) return BSP_ENOMEM;
+    cudaError_t e = launch_density(g, pos, n_particles, box, ws, (cx<float>*)delta_k, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "density (CIC + forward FFT)");
+    if (nbar) *nbar = (double)n_particles / (box * box * box);
+    return BSP_OK;
+}
+
 bsp_status bsp_last_raw(const bsp_plan* p, void* ws, void* stream, double* T) {
     if (!p || !ws || !T || !aligned256(ws)) return BSP_EINVAL;
     if (!p->have_counts) return BSP_ESTATE;

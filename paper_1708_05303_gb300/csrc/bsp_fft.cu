@@ -22,6 +22,8 @@
 // autosort radix-2/3/4/5/8 stages, ping-ponging between two shared-memory
 // buffers with one barrier per stage.  Twiddles come from a host table of
 // exp(+2 pi i t/N) computed in FP64.
+#include <algorithm>
+
 #include "bsp_internal.h"
 
 namespace bsp {
@@ -568,6 +570,203 @@ cudaError_t launch_n(const FftGeom& g, const cx<float>* delta, const int16_t* sh
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Density input stage: cloud-in-cell with interlacing, then a forward
+// real-to-complex 3-D FFT of both grids, combined into delta(k).  The
+// forward transforms reuse the inverse Stockham stages through
+// FFT(x) = conj(IFFT(conj x)).
+// ---------------------------------------------------------------------------
+
+// CIC weights of every particle on grid 1 (cells at j H) and grid 2 (cells at
+// (j + 1/2) H): positions to cell units and fractions in FP64, weights added
+// with FP32 atomics.
+__global__ void k_cic(const float* __restrict__ pos, long long np, int n, double scale, float* __restrict__ g1,
+                      float* __restrict__ g2) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double p[3] = {(double)pos[3 * i], (double)pos[3 * i + 1], (double)pos[3 * i + 2]};
+#pragma unroll
+        for (int gs = 0; gs < 2; ++gs) {
+            float* g = gs ? g2 : g1;
+            int b[3];
+            float t[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double u = p[a] * scale - 0.5 * gs;
+                u -= floor(u / n) * n;   // into [0, n)
+                int bi = (int)floor(u);
+                if (bi >= n) bi -= n;
+                if (bi < 0) bi += n;
+                b[a] = bi;
+                t[a] = (float)(u - (double)bi);
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int ox = (c >> 2) & 1, oy = (c >> 1) & 1, oz = c & 1;
+                const float w = (ox ? t[0] : 1.f - t[0]) * (oy ? t[1] : 1.f - t[1]) * (oz ? t[2] : 1.f - t[2]);
+                const int ix = (b[0] + ox) % n, iy = (b[1] + oy) % n, iz = (b[2] + oz) % n;
+                atomicAdd(&g[((size_t)ix * n + iy) * n + iz], w);
+            }
+        }
+    }
+}
+
+// exp(+2 pi i t / n), t < n, from FP64 sincospi.
+__global__ void k_twiddles(int n, cx<float>* __restrict__ tw) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)t / (double)n, &s, &c);
+    tw[t] = cx<float>{(float)c, (float)s};
+}
+
+// z pass: P real lines (x fixed, y0 .. y0 + P - 1) of grid blockIdx.y, with
+// delta = a g + b applied on load, packed as z_m = d_{2m} + i d_{2m+1}; an
+// M = n/2-point FFT gives Z; X_k = E_k + e^{-2 pi i k/n} O_k with
+// E_k = (Z_k + conj Z_{M-k})/2, O_k = (Z_k - conj Z_{M-k})/(2i), k = 0 .. M.
+template <int P, int NN>
+__global__ void __launch_bounds__(NTHR) k_fwd_z(FftGeom g, const float* __restrict__ grid, size_t gstride, float a,
+                                                float b, const cx<float>* __restrict__ twg, cx<float>* __restrict__ T,
+                                                size_t tstride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = NN ? NN : g.n, M = N / 2, H = M + 1;
+    cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+    cx<float>* buf = tw + N;
+    cx<float>* scr = buf + smem_elems<false, P>(M);
+    const int nyb = (N + P - 1) / P;
+    const int x = blockIdx.x / nyb, y0 = (blockIdx.x % nyb) * P;
+    const float* src = grid + (size_t)blockIdx.y * gstride;
+    for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
+    for (int e = threadIdx.x; e < M * P; e += NTHR) {
+        const int m = e % M, p = e / M, y = y0 + p;
+        cx<float> v = {0.f, 0.f};
+        if (y < N) {
+            const float2 r = *reinterpret_cast<const float2*>(src + ((size_t)x * N + y) * N + 2 * m);
+            v = cx<float>{a * r.x + b, -(a * r.y + b)};   // conjugated
+        }
+        buf[sidx<false, P>(p, m, M)] = v;
+    }
+    __syncthreads();
+    const cx<float>* res;
+    if constexpr (NN > 0) res = fft_ct<float, false, P, NN / 2>(buf, scr, tw, 2);
+    else res = fft_pingpong<float, false, P>(buf, scr, M, g.rad_h, g.nrad_h, tw, 2);
+    cx<float>* dst = T + (size_t)blockIdx.y * tstride;
+    for (int e = threadIdx.x; e < H * P; e += NTHR) {
+        const int k = e % H, p = e / H, y = y0 + p;
+        if (y >= N) continue;
+        const cx<float> rk = res[sidx<false, P>(p, k % M, M)], rm = res[sidx<false, P>(p, (M - k) % M, M)];
+        const cx<float> zk = {rk.re, -rk.im}, czm = {rm.re, rm.im};   // Z_k, conj Z_{M-k}
+        const cx<float> E = cscale(cadd(zk, czm), 0.5f);
+        const cx<float> D = cscale(csub(zk, czm), 0.5f);
+        const cx<float> O = {D.im, -D.re};                               // D / i
+        const cx<float> w = {tw[k].re, -tw[k].im};                       // e^{-2 pi i k/n}
+        dst[((size_t)x * N + y) * H + k] = cadd(E, cmul(w, O));
+    }
+}
+
+// y or x pass, in place: P consecutive k_z of one row o of grid blockIdx.y,
+// element j at o * so + j * sj + k_z.
+template <int P, int NN>
+__global__ void __launch_bounds__(NTHR) k_fwd_axis(FftGeom g, const cx<float>* __restrict__ twg, cx<float>* T,
+                                                   size_t tstride, size_t so, size_t sj) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = NN ? NN : g.n, H = N / 2 + 1;
+    cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+    cx<float>* buf = tw + N;
+    cx<float>* scr = buf + smem_elems<true, P>(N);
+    const int nkzb = (H + P - 1) / P;
+    const int o = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P;
+    cx<float>* t = T + (size_t)blockIdx.y * tstride;
+    for (int q = threadIdx.x; q < N; q += NTHR) tw[q] = twg[q];
+    for (int e = threadIdx.x; e < N * P; e += NTHR) {
+        const int p = e % P, j = e / P, kz = kz0 + p;
+        cx<float> v = {0.f, 0.f};
+        if (kz < H) {
+            const cx<float> u = t[(size_t)o * so + (size_t)j * sj + kz];
+            v = cx<float>{u.re, -u.im};
+        }
+        buf[sidx<true, P>(p, j, N)] = v;
+    }
+    __syncthreads();
+    const cx<float>* res;
+    if constexpr (NN > 0) res = fft_ct<float, true, P, NN>(buf, scr, tw, 1);
+    else res = fft_pingpong<float, true, P>(buf, scr, N, g.rad, g.nrad, tw, 1);
+    for (int e = threadIdx.x; e < N * P; e += NTHR) {
+        const int p = e % P, j = e / P, kz = kz0 + p;
+        if (kz < H) {
+            const cx<float> r = res[sidx<true, P>(p, j, N)];
+            t[(size_t)o * so + (size_t)j * sj + kz] = cx<float>{r.re, -r.im};
+        }
+    }
+}
+
+// delta(k) = (V/n^3) [X1(k) + e^{-i pi (n_x+n_y+n_z)/n} X2(k)] / (2 W(k)),
+// W = prod_a sinc^2(pi n_a / n).
+__global__ void k_fwd_combine(int N, const cx<float>* __restrict__ T1, const cx<float>* __restrict__ T2, float scale,
+                              cx<float>* __restrict__ out) {
+    const int H = N / 2 + 1;
+    const size_t total = (size_t)N * N * H;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int kz = (int)(i % H), y = (int)((i / H) % N), x = (int)(i / ((size_t)H * N));
+        const int fx = x < N / 2 ? x : x - N, fy = y < N / 2 ? y : y - N, fz = kz == N / 2 ? -(N / 2) : kz;
+        float s, c;
+        sincospif(-(float)(fx + fy + fz) / (float)N, &s, &c);
+        float W = 1.f;
+        const int f3[3] = {fx, fy, fz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (f3[a] != 0) {
+                const float u = (float)f3[a] / (float)N;
+                const float sc = sinpif(u) / (3.14159265358979f * u);
+                W *= sc * sc;
+            }
+        const cx<float> a1 = T1[i], a2 = T2[i];
+        const cx<float> ph = {c, s};
+        out[i] = cscale(cadd(a1, cmul(ph, a2)), 0.5f * scale / W);
+    }
+}
+
+template <int NN>
+cudaError_t launch_density_n(const FftGeom& g, const float* pos, long long np, double box, char* ws,
+                             cx<float>* out, cudaStream_t st) {
+    constexpr int P = 8;
+    const int N = g.n, M = N / 2, H = M + 1;
+    const DensityLayout L = density_layout(N);
+    cx<float>* tw = reinterpret_cast<cx<float>*>(ws + L.tw);
+    float* grids = reinterpret_cast<float*>(ws + L.grids);
+    cx<float>* T = reinterpret_cast<cx<float>*>(ws + L.spec);
+    const size_t gstride = (size_t)N * N * N, tstride = (size_t)N * N * H;
+    const size_t smz = sizeof(cx<float>) * ((size_t)N + 2 * (size_t)smem_elems<false, P>(M));
+    const size_t sma = sizeof(cx<float>) * ((size_t)N + 2 * (size_t)smem_elems<true, P>(N));
+    static size_t setz = 0, seta = 0;   // raised once per size, never inside a graph capture
+    cudaError_t e;
+    if (smz > setz) {
+        if ((e = cudaFuncSetAttribute(k_fwd_z<P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz)) !=
+            cudaSuccess)
+            return e;
+        setz = smz;
+    }
+    if (sma > seta) {
+        if ((e = cudaFuncSetAttribute(k_fwd_axis<P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma)) !=
+            cudaSuccess)
+            return e;
+        seta = sma;
+    }
+    if ((e = cudaMemsetAsync(grids, 0, 2 * gstride * sizeof(float), st)) != cudaSuccess) return e;
+    k_twiddles<<<(N + 255) / 256, 256, 0, st>>>(N, tw);
+    const int cic_blocks = (int)std::min<long long>(4096, (np + 255) / 256);
+    k_cic<<<cic_blocks, 256, 0, st>>>(pos, np, N, (double)N / box, grids, grids + gstride);
+    // delta_g = count / (N_p / n^3) - 1
+    const float a = (float)((double)gstride / (double)np);
+    k_fwd_z<P, NN><<<dim3(N * ((N + P - 1) / P), 2), NTHR, smz, st>>>(g, grids, gstride, a, -1.f, tw, T, tstride);
+    const int nkzb = (H + P - 1) / P;
+    k_fwd_axis<P, NN><<<dim3(N * nkzb, 2), NTHR, sma, st>>>(g, tw, T, tstride, (size_t)N * H, (size_t)H);   // along y
+    k_fwd_axis<P, NN><<<dim3(N * nkzb, 2), NTHR, sma, st>>>(g, tw, T, tstride, (size_t)H, (size_t)N * H);   // along x
+    const double V = box * box * box;
+    k_fwd_combine<<<4096, 256, 0, st>>>(N, T, T + tstride, (float)(V / (double)gstride), out);
+    return cudaGetLastError();
+}
 }  // namespace
 
 // Sizes of the workloads get kernels specialised at compile time; any other
@@ -600,6 +799,31 @@ template cudaError_t launch_fft_fields<float>(const FftGeom&, const cx<float>*, 
                                               const FieldDesc*, int, const cx<float>*, cx<float>*,
                                               cx<float>*, float*, size_t, uint32_t*, uint32_t*, int, unsigned*, unsigned*,
                                               cudaStream_t, FieldLayout);
+DensityLayout density_layout(int n) {
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    DensityLayout L{};
+    const size_t n3 = (size_t)n * n * n, nh = (size_t)n * n * (n / 2 + 1);
+    L.tw = 0;
+    L.grids = r256(sizeof(cx<float>) * (size_t)n);
+    L.spec = L.grids + r256(2 * n3 * sizeof(float));
+    L.end = L.spec + r256(2 * nh * sizeof(cx<float>));
+    return L;
+}
+
+cudaError_t launch_density(const FftGeom& g, const float* pos, long long np, double box, void* ws,
+                           cx<float>* out, cudaStream_t st) {
+    char* w = reinterpret_cast<char*>(ws);
+    switch (g.n) {
+        case 64: return launch_density_n<64>(g, pos, np, box, w, out, st);
+        case 96: return launch_density_n<96>(g, pos, np, box, w, out, st);
+        case 128: return launch_density_n<128>(g, pos, np, box, w, out, st);
+        case 160: return launch_density_n<160>(g, pos, np, box, w, out, st);
+        case 256: return launch_density_n<256>(g, pos, np, box, w, out, st);
+        case 512: return launch_density_n<512>(g, pos, np, box, w, out, st);
+        default: return launch_density_n<0>(g, pos, np, box, w, out, st);
+    }
+}
+
 template cudaError_t launch_fft_fields<double>(const FftGeom&, const cx<float>*, const int16_t*, const float*,
                                                const FieldDesc*, int, const cx<double>*, cx<double>*,
                                                cx<double>*, double*, size_t, uint32_t*, uint32_t*, int,

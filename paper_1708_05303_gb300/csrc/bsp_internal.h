@@ -140,6 +140,14 @@ cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_ro
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
                                unsigned* pace, cudaStream_t st);
 
+// ---- density input stage (bsp_fft.cu) ----
+struct DensityLayout {   // byte offsets in the caller's workspace
+    size_t tw, grids, spec, end;
+};
+DensityLayout density_layout(int n);
+cudaError_t launch_density(const FftGeom& g, const float* pos, long long np, double box, void* ws,
+                           cx<float>* out, cudaStream_t st);
+
 // ---- launchers (bsp_power.cu) ----
 struct PowerEll {   // the multipoles of a power-spectrum call (even l in {0, 2, 4})
     int n;

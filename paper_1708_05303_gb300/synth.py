@@ -150,6 +150,25 @@ def cic_interlaced(model: FieldModel, seed: int, n_particles: int = 4 * 2 ** 20,
     return d.astype(dtype), npart, nbar
 
 
+def poisson_positions(model: FieldModel, seed: int, n_particles: int = 4 * 2 ** 20) -> np.ndarray:
+    """Particle positions (float32 [N_p][3], box units in [0, box)) of the
+    particle workload: lognormal rate from ``make_field`` as in
+    ``cic_interlaced``, Poisson counts per cell, uniform within the cell."""
+    n, box = model.n, model.box
+    dk, _ = make_field(model, seed, dtype=np.complex128)
+    ds = np.fft.irfftn(dk * (n ** 3 / box ** 3), s=(n, n, n), axes=(0, 1, 2))
+    lam = np.exp(ds - ds.max())
+    lam *= n_particles / lam.sum()
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    cnt = rng.poisson(lam).ravel()
+    cell = np.repeat(np.arange(n ** 3), cnt)
+    cx, cy, cz = np.unravel_index(cell, (n, n, n))
+    pos = np.stack([cx, cy, cz], axis=1).astype(np.float64)
+    pos += rng.random((pos.shape[0], 3))
+    pos *= box / n
+    return np.minimum(pos, np.nextafter(box, 0)).astype(np.float32) % np.float32(box)
+
+
 def linear_edges(n_shells: int, width: float = 2.0, start: float = 1.0):
     """Shell edges in k_f units: start + width*i, i = 0..n_shells."""
     return [start + width * i for i in range(n_shells + 1)]
