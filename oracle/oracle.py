@@ -43,7 +43,7 @@ __all__ = [
     "brute_triangles", "candidate_triplets", "counts", "bispectrum",
     "shot_noise", "modal_q", "modal_radial", "modal_fields", "modal_triplets",
     "modal_raw", "modal_mode_order", "modal_gamma", "modal_beta", "covariance",
-    "power_multipoles", "density_from_particles",
+    "power_multipoles", "density_from_particles", "skew_spectrum",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -631,3 +631,37 @@ def density_from_particles(pos: np.ndarray, n: int, box: float):
     phase = np.exp(-1j * np.pi / n * (f[:, None, None] + f[None, :, None] + fz[None, None, :]))
     win = (np.sinc(f / n)[:, None, None] * np.sinc(f / n)[None, :, None] * np.sinc(fz / n)[None, None, :]) ** 2
     return 0.5 * (out[0] + phase * out[1]) / win, npart / V
+
+
+# ----------------------------------------------------------------------------
+# Skew-spectrum multipoles (Sec. 3.3, Eq. skewspecQ with Q the convolution)
+# ----------------------------------------------------------------------------
+
+def skew_spectrum(delta_half: np.ndarray, n: int, box: float, edges, ells=(0, 2, 4)):
+    """S_{*,l}(k): the direction average over shell a of [delta * delta](-k)
+    delta^(l)(k), the convolution being the transform of delta(x)^2 (Sec. 3.3,
+    the estimator under Eq. skewspecQ).  Normalised with 1/V like P^(l), so
+    that its mean is int d^3q/(2 pi)^3 B^(l)(k, q, |k+q|):
+
+        S^l_a = 1/(V N_a) sum_{n in a} w_l(mu_n) Re[conj Q(n) delta(n)],
+        Q(n) = (V/n^3) sum_x delta_x^2 e^{-ik.x},  delta_x = (1/V) sum_n delta(n) e^{ik.x},
+
+    delta the Hermitian spectrum with its mean mode removed (delta(0) = 0);
+    no dealiasing of the square on the grid.  Returns dict(S [n_ell][n_shells], Nk)."""
+    V = float(box) ** 3
+    full = full_from_half(delta_half, n)
+    full[0, 0, 0] = 0.0
+    dx = np.real(np.fft.ifftn(full)) * (n ** 3 / V)
+    Q = np.fft.fftn(dx * dx) * (V / n ** 3)
+    cross = np.real(np.conj(Q) * full)
+    mu = mu_grid(n)
+    masks = shell_masks(n, edges)
+    S = np.zeros((len(ells), len(masks)))
+    Nk = np.zeros(len(masks))
+    for a, m in enumerate(masks):
+        Nk[a] = float(m.sum())
+        if Nk[a] == 0:
+            continue
+        for li, ell in enumerate(ells):
+            S[li, a] = float(np.sum(legendre_weight(ell, mu[m]) * cross[m])) / (V * Nk[a])
+    return dict(S=S, Nk=Nk)

@@ -526,3 +526,61 @@ def test_density_plane_wave_amplitude(ora):
     d, _ = ora.density_from_particles(P, n, box)
     want = box ** 3 * A / 2
     assert abs(d[m, 0, 0] - want) <= 0.01 * want
+
+
+# ---------------------------------------------------------------------------
+# Skew-spectrum multipoles (Sec. 3.3, Eq. skewspecQ)
+# ---------------------------------------------------------------------------
+
+def test_skew_parseval(ora):
+    """One shell holding every nonzero mode: V N S^0 = sum_n conj Q(n) delta(n),
+    which Parseval's theorem fixes as (V^2/n^3) sum_x delta_x^3 (zero mean)."""
+    from paper_1708_05303_gb300.synth import delta_k_from_real
+
+    n, box = 16, 1000.0
+    V = box ** 3
+    x = np.random.default_rng(5).standard_normal((n, n, n))
+    x -= x.mean()
+    r = ora.skew_spectrum(delta_k_from_real(x, box), n, box, [1, 3 ** 0.5 * n / 2 + 1], ells=(0,))
+    lhs = r["S"][0, 0] * V * r["Nk"][0]
+    rhs = V * V / n ** 3 * np.sum(x ** 3)
+    assert abs(lhs - rhs) <= 1e-12 * abs(rhs)
+
+
+def test_skew_brute_force_convolution(ora):
+    """On a 6^3 grid the convolution Q(n) = (1/V) sum_q delta(q) delta(n - q)
+    summed directly over all q (mod n) gives the same multipoles."""
+    from paper_1708_05303_gb300.synth import delta_k_from_real
+
+    n, box = 6, 1000.0
+    V = box ** 3
+    x = np.random.default_rng(6).standard_normal((n, n, n))
+    x -= x.mean()
+    dk = delta_k_from_real(x, box)
+    full = ora.full_from_half(dk, n)
+    full[0, 0, 0] = 0
+    idx = np.arange(n)
+    Q = np.zeros((n, n, n), complex)
+    for a in range(n):
+        for b in range(n):
+            for c in range(n):
+                sh = full[np.ix_((a - idx) % n, (b - idx) % n, (c - idx) % n)]
+                Q[a, b, c] = np.sum(full * sh) / V
+    mu = ora.mu_grid(n)
+    edges = [1, 2, 3, 4.5]
+    want = np.array([[np.sum(ora.legendre_weight(l, mu[m]) * np.real(np.conj(Q[m]) * full[m])) / (V * m.sum())
+                      for m in ora.shell_masks(n, edges)] for l in (0, 2, 4)])
+    got = ora.skew_spectrum(dk, n, box, edges)["S"]
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_skew_sign_follows_the_quadratic_term(ora):
+    """delta = g + b (g^2 - <g^2>): the large-scale skew spectrum has the sign
+    of b (tree level: B > 0 for b > 0), and flips with it."""
+    from paper_1708_05303_gb300.synth import FieldModel, make_field
+
+    out = []
+    for quad in (0.5, -0.5):
+        dk, _ = make_field(FieldModel(n=32, box=1000.0, quad=quad, f=0.0, sigma_g=0.3), 77, dtype=np.complex128)
+        out.append(ora.skew_spectrum(dk, 32, 1000.0, [1, 5, 9], ells=(0,))["S"][0])
+    assert np.all(out[0] > 0) and np.all(out[1] < 0)
