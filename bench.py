@@ -265,6 +265,22 @@ def main():
         Kp += 1
     nKp, nKzp = (min(args.n, 2 * Kp + 1), min(args.n // 2 + 1, Kp + 1))
     pw_bytes = nKp * nKp * nKzp * 8.0
+    # skew-spectrum multipoles on the same shells: inverse FFT of delta, square,
+    # forward FFT, shell-averaged cross spectrum (separate workspace)
+    import ctypes as _ct
+    _sb = _ct.c_size_t()
+    bsp.load().bsp_skew_workspace_size(est.plan, _ct.byref(_sb))
+    sws = torch.empty(_sb.value, dtype=torch.uint8, device="cuda")
+    est.skew(d, ws=sws)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(5):
+        est.skew(d, ws=sws)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    sk_ms = s0.elapsed_time(s1) / 5
+    del sws
     # density input stage (CIC + interlacing + forward FFT) on the particle workload's
     # shape: 256^3 grid, 4 Mi particles (uniform positions: the cost does not depend on them)
     dn, dnp = 256, 4 * 2 ** 20
@@ -273,7 +289,6 @@ def main():
     dws = None
     _, _ = bsp.density_from_particles(dpos, dn, BOX)
     torch.cuda.synchronize()
-    import ctypes as _ct
     _nb = _ct.c_size_t()
     bsp.load().bsp_density_workspace_size(dn, _ct.byref(_nb))
     dws = torch.empty(_nb.value, dtype=torch.uint8, device="cuda")
@@ -370,6 +385,7 @@ def main():
                               "particles_per_s": dnp / (den_ms / 1e3), "algorithmic_bytes": den_bytes,
                               "achieved_gbs": den_bytes / (den_ms / 1e3) / 1e9,
                               "frac_hbm": den_bytes / (den_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
+            "skew_spectrum": {"ms": sk_ms, "shells_per_s": args.shells * 3 / (sk_ms / 1e3)},
             "power_multipoles": {"ms": pw_ms, "shells_per_s": args.shells * 3 / (pw_ms / 1e3),
                                  "algorithmic_bytes": pw_bytes, "achieved_gbs": pw_bytes / (pw_ms / 1e3) / 1e9,
                                  "frac_hbm": pw_bytes / (pw_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}}

@@ -291,6 +291,24 @@ bsp_status bsp_density_workspace_size(int n, size_t* bytes);
 bsp_status bsp_density_cic(int n, double box, long long n_particles, const float* pos, void* ws, size_t ws_bytes,
                            void* stream, void* delta_k, double* nbar);
 
+/*
+ * Skew-spectrum multipoles on the plan's shells (Sec. 3.3, the estimator
+ * under Eq. skewspecQ with Q the convolution):
+ *   S^l_a = 1/(V N_a) sum_{n in a} w_l(mu_n) Re[conj Q(n) delta(n)],
+ *   Q = transform of delta(x)^2, delta(x) from every mode but the mean,
+ * i.e. the shell average of [delta * delta](-k) delta^(l)(k), normalised by
+ * 1/V like P^(l) so that its mean is int d^3q/(2 pi)^3 B^(l)(k, q, |k+q|).
+ *   delta_k: device complex64 [n][n][n/2+1].
+ *   ws:      device workspace of bsp_skew_workspace_size bytes (~20 n^3),
+ *            256-byte aligned, separate from the plan's; ws_bytes its size.
+ *   S:       device FP64 [n_ell][n_shells] (out); Nk as for bsp_power_compute.
+ * Asynchronous on `stream`; deterministic.  Standard plans only; n even with
+ * n and n/2 of the form 2^a 3^b 5^c.
+ */
+bsp_status bsp_skew_workspace_size(const bsp_plan* plan, size_t* bytes);
+bsp_status bsp_skew_compute(bsp_plan* plan, const void* delta_k, void* ws, size_t ws_bytes, void* stream, double* S,
+                            double* Nk);
+
 /* Raw sums T^l = sum_x F^l_a F_b F_c of the last bsp_compute (FP64
  * [n_ell][n_bins], device), copied into T (device).  For tests. */
 bsp_status bsp_last_raw(const bsp_plan* plan, void* ws, void* stream, double* T);

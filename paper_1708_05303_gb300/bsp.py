@@ -50,6 +50,8 @@ _SIGS = [
     ("bsp_last_raw", ctypes.c_int, [_P, _P, _P, _P]),
     ("bsp_power_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P, _P]),
     ("bsp_density_workspace_size", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    ("bsp_skew_workspace_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    ("bsp_skew_compute", ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
     ("bsp_density_cic", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_longlong, _P, _P, ctypes.c_size_t, _P,
                                        _P, ctypes.POINTER(ctypes.c_double)]),
     ("bsp_device_status", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
@@ -459,6 +461,22 @@ class Bispectrum:
         Nk = torch.empty(len(self.edges) - 1, dtype=torch.float64, device="cuda")
         bsp_power_compute(self.plan, delta_k, P, self.ws, nbar, stream, Nk)
         return P, Nk
+
+    def skew(self, delta_k, ws=None, stream=None):
+        """Skew-spectrum multipoles S [n_ell][n_shells] and mode counts Nk (FP64,
+        device) on the plan's shells; ``ws`` an optional reusable uint8 CUDA
+        tensor of bsp_skew_workspace_size bytes."""
+        import torch
+
+        nb = ctypes.c_size_t()
+        _check(load().bsp_skew_workspace_size(self.plan, ctypes.byref(nb)), "bsp_skew_workspace_size")
+        if ws is None or ws.numel() < nb.value:
+            ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+        S = torch.empty((len(self.ells), len(self.edges) - 1), dtype=torch.float64, device="cuda")
+        Nk = torch.empty(len(self.edges) - 1, dtype=torch.float64, device="cuda")
+        _check(load().bsp_skew_compute(self.plan, _dptr(delta_k), _dptr(ws), int(ws.numel()), _stream_handle(stream),
+                                       _dptr(S), _dptr(Nk)), "bsp_skew_compute")
+        return S, Nk
 
     def raw(self, stream=None):
         import torch

@@ -335,6 +335,7 @@ struct bsp_plan {
     int target_ctas = 2048;
     int fb_cap = 1;                   // FFT batch width the workspace was sized for
     int16_t* d_shell_of = nullptr;
+    FieldDesc* d_fd_raw = nullptr;    // one field: delta on every mode but the mean (skew spectrum)
     cx<float>* d_tw32 = nullptr;
     cx<double>* d_tw64 = nullptr;
     FieldDesc* d_fd_delta = nullptr;  // [nslot*nsh], or [3][nslot*nsh] with shot noise
@@ -392,7 +393,7 @@ struct bsp_plan {
 
     ~bsp_plan() {
         for (auto e : ev_pool) cudaEventDestroy(e);
-        cudaFree(d_shell_of); cudaFree(d_tw32); cudaFree(d_tw64);
+        cudaFree(d_shell_of); cudaFree(d_tw32); cudaFree(d_tw64); cudaFree(d_fd_raw);
         cudaFree(d_fd_delta); cudaFree(d_fd_unit); cudaFree(d_counts);
         cudaFree(d_fd_tc); cudaFree(d_tc_works); cudaFree(d_tc_pairs); cudaFree(d_tc_loc); cudaFree(d_err);
         cudaFree(d_fmax);
@@ -597,6 +598,7 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     if ((st = upload(&p->d_shell_of, shell_of)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||
         (st = upload(&p->d_tw64, tw64)) != BSP_OK || (st = upload(&p->d_fd_delta, fdd)) != BSP_OK ||
         (st = upload(&p->d_fd_unit, fdu)) != BSP_OK || (st = upload(&p->d_fd_tc, fdt)) != BSP_OK ||
+        (st = upload(&p->d_fd_raw, std::vector<FieldDesc>{FieldDesc{0, 0, FIELD_RAW, 0, -1, {0, 0, 0}}})) != BSP_OK ||
         (st = upload(&p->d_err, std::vector<int>{0, 0, 0})) != BSP_OK ||
         (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)p->nslot() * pad16 + n_shells, 0u))) != BSP_OK) {
         delete p;
@@ -1264,7 +1266,8 @@ bsp_status bsp_power_compute(bsp_plan* p, const void* delta_k, double nbar, void
     while (nblocks > 1 && power_partial_bytes(nblocks, p->nsh, pe.n) > p->ws_bytes) nblocks /= 2;
     if (power_partial_bytes(nblocks, p->nsh, pe.n) > p->ws_bytes) return BSP_ENOMEM;
     const double V = p->box * p->box * p->box;
-    cudaError_t e = launch_power((const cx<float>*)delta_k, p->geom, p->d_shell_of, p->nsh, pe, V, nbar, nblocks,
+    cudaError_t e = launch_power((const cx<float>*)delta_k, nullptr, 1.0, p->geom, p->d_shell_of, p->nsh, pe, V, nbar,
+                                 nblocks,
                                  (double*)ws, P, Nk, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "power multipoles");
     return BSP_OK;
@@ -1298,6 +1301,59 @@ bsp_status bsp_density_cic(int n, double box, long long n_particles, const float
     cudaError_t e = launch_density(g, pos, n_particles, box, ws, (cx<float>*)delta_k, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "density (CIC + forward FFT)");
     if (nbar) *nbar = (double)n_particles / (box * box * box);
+    return BSP_OK;
+}
+
+// Skew-spectrum workspace: the real field x [n^3] FP32, then two unpruned
+// half spectra (the inverse FFT's intermediates, reused for the transform of
+// x^2 and for the per-CTA sums).
+static size_t skew_bytes(int n, size_t* off_t1, size_t* off_t2) {
+    const size_t x = round256((size_t)n * n * n * sizeof(float));
+    const size_t h = round256((size_t)n * n * (n / 2 + 1) * sizeof(cx<float>));
+    if (off_t1) *off_t1 = x;
+    if (off_t2) *off_t2 = x + h;
+    return x + 2 * h;
+}
+
+bsp_status bsp_skew_workspace_size(const bsp_plan* p, size_t* bytes) {
+    if (!p || !bytes || p->modal) return BSP_EINVAL;
+    *bytes = skew_bytes(p->n, nullptr, nullptr);
+    return BSP_OK;
+}
+
+bsp_status bsp_skew_compute(bsp_plan* p, const void* delta_k, void* ws, size_t ws_bytes, void* stream, double* S,
+                            double* Nk) {
+    if (!p || !delta_k || !ws || !S || !aligned256(ws)) return BSP_EINVAL;
+    if (p->modal || p->nsh <= 0 || p->ells.size() > 3 || !p->d_fd_raw) return BSP_EINVAL;
+    FftGeom full;
+    if (!density_geom(p->n, &full)) return BSP_EUNSUPPORTED;
+    size_t o1, o2;
+    if (ws_bytes < skew_bytes(p->n, &o1, &o2)) return BSP_ENOMEM;
+    const cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    float* x = (float*)base;
+    cx<float>* t1 = (cx<float>*)(base + o1);
+    cx<float>* t2 = (cx<float>*)(base + o2);
+    const size_t n3 = (size_t)p->n * p->n * p->n;
+    // x = sum_{n != 0} delta(n) e^{ik.x} = V delta(x)
+    cudaError_t e = launch_fft_fields<float>(full, (const cx<float>*)delta_k, p->d_shell_of, nullptr, p->d_fd_raw, 1,
+                                             p->d_tw32, t1, t2, x, n3, nullptr, nullptr, 0, nullptr, nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "skew (inverse FFT)");
+    // transform of delta(x)^2 = x^2 / V^2, unnormalised, into t1
+    const double V = p->box * p->box * p->box;
+    e = launch_forward_square(full, x, (float)(1.0 / (V * V)), p->d_tw32, t1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "skew (forward FFT)");
+    PowerEll pe{};
+    pe.n = (int)p->ells.size();
+    for (int i = 0; i < pe.n; ++i) pe.ell[i] = p->ells[i];
+    const long long rows = (long long)p->geom.nK * p->geom.nK;
+    int nblocks = (int)std::min<long long>(rows, 4LL * p->nsm);
+    const size_t room = (size_t)(ws_bytes - o2);
+    while (nblocks > 1 && power_partial_bytes(nblocks, p->nsh, pe.n) > room) nblocks /= 2;
+    // Q = (V/n^3) x transform: the cross sum carries that factor
+    e = launch_power((const cx<float>*)delta_k, t1, V / (double)n3, p->geom, p->d_shell_of, p->nsh, pe, V, 0.0,
+                     nblocks, (double*)t2, S, Nk, st);
+    if (e != cudaSuccess) return cuda_fail(e, "skew (shell sums)");
     return BSP_OK;
 }
 

@@ -225,6 +225,7 @@ __device__ __forceinline__ R filter_weight(const FieldDesc& fd, int n2, int fz, 
                                            const float* radial, int n2max) {
     if (n2 <= 0 || n2 > n2max) return (R)0;
     R base;
+    if (fd.kind == FIELD_RAW) return (R)1;
     if (fd.kind == FIELD_RADIAL) base = (R)radial[(size_t)fd.shell * (n2max + 1) + n2];
     else base = (shell_of[n2] == fd.shell) ? (R)1 : (R)0;
     if (base == (R)0 || fd.ell == 0) return base;
@@ -625,7 +626,7 @@ __global__ void k_twiddles(int n, cx<float>* __restrict__ tw) {
 // delta = a g + b applied on load, packed as z_m = d_{2m} + i d_{2m+1}; an
 // M = n/2-point FFT gives Z; X_k = E_k + e^{-2 pi i k/n} O_k with
 // E_k = (Z_k + conj Z_{M-k})/2, O_k = (Z_k - conj Z_{M-k})/(2i), k = 0 .. M.
-template <int P, int NN>
+template <int P, int NN, bool SQ = false>
 __global__ void __launch_bounds__(NTHR) k_fwd_z(FftGeom g, const float* __restrict__ grid, size_t gstride, float a,
                                                 float b, const cx<float>* __restrict__ twg, cx<float>* __restrict__ T,
                                                 size_t tstride) {
@@ -643,7 +644,8 @@ __global__ void __launch_bounds__(NTHR) k_fwd_z(FftGeom g, const float* __restri
         cx<float> v = {0.f, 0.f};
         if (y < N) {
             const float2 r = *reinterpret_cast<const float2*>(src + ((size_t)x * N + y) * N + 2 * m);
-            v = cx<float>{a * r.x + b, -(a * r.y + b)};   // conjugated
+            const float r0 = SQ ? r.x * r.x : r.x, r1 = SQ ? r.y * r.y : r.y;
+            v = cx<float>{a * r0 + b, -(a * r1 + b)};   // conjugated
         }
         buf[sidx<false, P>(p, m, M)] = v;
     }
@@ -808,6 +810,48 @@ DensityLayout density_layout(int n) {
     L.spec = L.grids + r256(2 * n3 * sizeof(float));
     L.end = L.spec + r256(2 * nh * sizeof(cx<float>));
     return L;
+}
+
+template <int NN>
+cudaError_t launch_forward_square_n(const FftGeom& g, const float* x, float a, const cx<float>* tw, cx<float>* T,
+                                    cudaStream_t st) {
+    constexpr int P = 8;
+    const int N = g.n, M = N / 2, H = M + 1;
+    const size_t smz = sizeof(cx<float>) * ((size_t)N + 2 * (size_t)smem_elems<false, P>(M));
+    const size_t sma = sizeof(cx<float>) * ((size_t)N + 2 * (size_t)smem_elems<true, P>(N));
+    static size_t setz = 0, seta = 0;   // raised once per size, never inside a graph capture
+    cudaError_t e;
+    if (smz > setz) {
+        if ((e = cudaFuncSetAttribute(k_fwd_z<P, NN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smz)) != cudaSuccess)
+            return e;
+        setz = smz;
+    }
+    if (sma > seta) {
+        if ((e = cudaFuncSetAttribute(k_fwd_axis<P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma)) !=
+            cudaSuccess)
+            return e;
+        seta = sma;
+    }
+    const size_t tstride = (size_t)N * N * H;
+    k_fwd_z<P, NN, true><<<dim3(N * ((N + P - 1) / P), 1), NTHR, smz, st>>>(g, x, 0, a, 0.f, tw, T, tstride);
+    const int nkzb = (H + P - 1) / P;
+    k_fwd_axis<P, NN><<<dim3(N * nkzb, 1), NTHR, sma, st>>>(g, tw, T, tstride, (size_t)N * H, (size_t)H);
+    k_fwd_axis<P, NN><<<dim3(N * nkzb, 1), NTHR, sma, st>>>(g, tw, T, tstride, (size_t)H, (size_t)N * H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_square(const FftGeom& g, const float* x, float a, const cx<float>* tw, cx<float>* T,
+                                  cudaStream_t st) {
+    switch (g.n) {
+        case 64: return launch_forward_square_n<64>(g, x, a, tw, T, st);
+        case 96: return launch_forward_square_n<96>(g, x, a, tw, T, st);
+        case 128: return launch_forward_square_n<128>(g, x, a, tw, T, st);
+        case 160: return launch_forward_square_n<160>(g, x, a, tw, T, st);
+        case 256: return launch_forward_square_n<256>(g, x, a, tw, T, st);
+        case 512: return launch_forward_square_n<512>(g, x, a, tw, T, st);
+        default: return launch_forward_square_n<0>(g, x, a, tw, T, st);
+    }
 }
 
 cudaError_t launch_density(const FftGeom& g, const float* pos, long long np, double box, void* ws,

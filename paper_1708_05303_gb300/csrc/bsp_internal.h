@@ -19,6 +19,7 @@ enum FieldKind : int {
     FIELD_UNIT = 1,     // w_l(mu) 1[n in shell]            (counts: delta == 1)
     FIELD_POWER = 2,    // w_l(mu) 1[n in shell] |delta(n)|^2  (shot noise)
     FIELD_RADIAL = 3,   // w_l(mu) R_p[n^2] delta(n)        (modal)
+    FIELD_RAW = 4,      // delta(n) on every mode but the mean (skew spectrum)
 };
 
 struct FieldDesc {
@@ -147,6 +148,10 @@ struct DensityLayout {   // byte offsets in the caller's workspace
 DensityLayout density_layout(int n);
 cudaError_t launch_density(const FftGeom& g, const float* pos, long long np, double box, void* ws,
                            cx<float>* out, cudaStream_t st);
+// Forward real-to-complex FFT (unnormalised, e^{-ik.x}) of a * x^2 for a real
+// field x [n][n][n]; spectrum T [n][n][n/2+1]; tw = exp(+2 pi i t/n), t < n.
+cudaError_t launch_forward_square(const FftGeom& g, const float* x, float a, const cx<float>* tw, cx<float>* T,
+                                  cudaStream_t st);
 
 // ---- launchers (bsp_power.cu) ----
 struct PowerEll {   // the multipoles of a power-spectrum call (even l in {0, 2, 4})
@@ -154,9 +159,11 @@ struct PowerEll {   // the multipoles of a power-spectrum call (even l in {0, 2,
     int ell[3];
 };
 size_t power_partial_bytes(int nblocks, int nsh, int nell);
-cudaError_t launch_power(const cx<float>* delta, const FftGeom& g, const int16_t* shell_of, int nsh,
-                         const PowerEll& ells, double V, double nbar, int nblocks, double* partial, double* P,
-                         double* Nk, cudaStream_t st);
+// P^l_a (Q == nullptr: w_l |delta|^2) or the cross spectrum (w_l Re conj(Q) delta,
+// Q in the half-spectrum layout of delta, multiplied by num_scale), over V N_a.
+cudaError_t launch_power(const cx<float>* delta, const cx<float>* Q, double num_scale, const FftGeom& g,
+                         const int16_t* shell_of, int nsh, const PowerEll& ells, double V, double nbar, int nblocks,
+                         double* partial, double* P, double* Nk, cudaStream_t st);
 
 // ---- launchers (bsp_modal.cu) ----
 cudaError_t launch_modal_assemble(const double* T, const double* U, const int* ells, int n_ell, int nf,

@@ -26,7 +26,8 @@ __device__ __forceinline__ float legendre_w(int ell, float mu2) {
 
 constexpr int PW_WARPS = 8;   // warps per CTA
 
-__global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>* __restrict__ delta, FftGeom g,
+__global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>* __restrict__ delta,
+                                                                 const cx<float>* __restrict__ Q, FftGeom g,
                                                                  const int16_t* __restrict__ shell_of, int nsh,
                                                                  PowerEll ells, double* __restrict__ partial) {
     // per warp [2 nell + 1][nsh] FP64: sum w|d|^2 per l, sum w per l, mode count
@@ -49,7 +50,8 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
         const int fy = g.pruned ? cy - g.K : (cy < N / 2 ? cy : cy - N);
         const int ix = (fx + N) % N, iy = (fy + N) % N;
         const cx<float>* row = delta + ((size_t)ix * N + iy) * H;
-        const cx<float>* mrow = delta + ((size_t)((N - ix) % N) * N + (N - iy) % N) * H;
+        const size_t mo = ((size_t)((N - ix) % N) * N + (N - iy) % N) * H, ro = ((size_t)ix * N + iy) * H;
+        const cx<float>* mrow = delta + mo;
         for (int k0 = 0; k0 < g.nKz; k0 += 32) {
             const int kz = k0 + lane;
             int s = -1;
@@ -67,7 +69,19 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
                         im = 0.5f * (im - m.im);
                         h = 1.f;
                     }
-                    const float p = h * (re * re + im * im), mu2 = (float)(fz * fz) / (float)n2;
+                    float p = re * re + im * im;
+                    if (Q) {   // cross spectrum: Re[conj(Q) delta], Hermitian parts on both
+                        const cx<float> q = Q[ro + kz];
+                        float qr = q.re, qi = q.im;
+                        if (kz == 0 || kz == N / 2) {
+                            const cx<float> qm = Q[mo + kz];
+                            qr = 0.5f * (qr + qm.re);
+                            qi = 0.5f * (qi - qm.im);
+                        }
+                        p = qr * re + qi * im;
+                    }
+                    p *= h;
+                    const float mu2 = (float)(fz * fz) / (float)n2;
                     for (int l = 0; l < nell; ++l) {
                         const float w = legendre_w(ells.ell[l], mu2);
                         v[l] = w * p;
@@ -108,7 +122,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
 }
 
 __global__ void k_power_final(const double* __restrict__ partial, int nblocks, int nsh, int nell, double V,
-                              double nbar, double* __restrict__ P, double* __restrict__ Nk) {
+                              double nbar, double num_scale, double* __restrict__ P, double* __restrict__ Nk) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nell * nsh) return;
     const int l = t / nsh, s = t % nsh, per = (2 * nell + 1) * nsh;
@@ -121,7 +135,7 @@ __global__ void k_power_final(const double* __restrict__ partial, int nblocks, i
     }
     double v = 0.0;
     if (sn > 0.0) {
-        v = sp / (V * sn);
+        v = num_scale * sp / (V * sn);
         if (nbar > 0.0) v -= sw / (nbar * sn);
     }
     P[t] = v;
@@ -134,9 +148,9 @@ size_t power_partial_bytes(int nblocks, int nsh, int nell) {
     return (size_t)nblocks * (size_t)(2 * nell + 1) * (size_t)nsh * sizeof(double);
 }
 
-cudaError_t launch_power(const cx<float>* delta, const FftGeom& g, const int16_t* shell_of, int nsh,
-                         const PowerEll& ells, double V, double nbar, int nblocks, double* partial, double* P,
-                         double* Nk, cudaStream_t st) {
+cudaError_t launch_power(const cx<float>* delta, const cx<float>* Q, double num_scale, const FftGeom& g,
+                         const int16_t* shell_of, int nsh, const PowerEll& ells, double V, double nbar, int nblocks,
+                         double* partial, double* P, double* Nk, cudaStream_t st) {
     const size_t smem = (size_t)PW_WARPS * (2 * ells.n + 1) * nsh * sizeof(double);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     static size_t set = 0;   // raised once per size, never inside a graph capture
@@ -147,9 +161,9 @@ cudaError_t launch_power(const cx<float>* delta, const FftGeom& g, const int16_t
             return e;
         set = smem;
     }
-    k_power_partial<<<nblocks, 32 * PW_WARPS, smem, st>>>(delta, g, shell_of, nsh, ells, partial);
+    k_power_partial<<<nblocks, 32 * PW_WARPS, smem, st>>>(delta, Q, g, shell_of, nsh, ells, partial);
     const int nt = ells.n * nsh;
-    k_power_final<<<(nt + 127) / 128, 128, 0, st>>>(partial, nblocks, nsh, ells.n, V, nbar, P, Nk);
+    k_power_final<<<(nt + 127) / 128, 128, 0, st>>>(partial, nblocks, nsh, ells.n, V, nbar, num_scale, P, Nk);
     return cudaGetLastError();
 }
 
