@@ -43,7 +43,7 @@ __all__ = [
     "brute_triangles", "candidate_triplets", "counts", "bispectrum",
     "shot_noise", "modal_q", "modal_radial", "modal_fields", "modal_triplets",
     "modal_raw", "modal_mode_order", "modal_gamma", "modal_beta", "covariance",
-    "power_multipoles", "density_from_particles", "skew_spectrum",
+    "power_multipoles", "density_from_particles", "skew_spectrum", "integrated_bispectrum",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -665,3 +665,43 @@ def skew_spectrum(delta_half: np.ndarray, n: int, box: float, edges, ells=(0, 2,
         for li, ell in enumerate(ells):
             S[li, a] = float(np.sum(legendre_weight(ell, mu[m]) * cross[m])) / (V * Nk[a])
     return dict(S=S, Nk=Nk)
+
+
+# ----------------------------------------------------------------------------
+# Integrated bispectrum multipoles (Sec. 3.4, the estimator after
+# Eq. iB_expectation, applied to the multipoles)
+# ----------------------------------------------------------------------------
+
+def integrated_bispectrum(delta_half: np.ndarray, n: int, box: float, edges, m: int, ells=(0, 2, 4)):
+    """iB^(l)(k) = (1/N_s) sum_i P^(l)(k)_i dbar_i over the N_s = m^3 cubes of
+    side n/m cells: delta(x) = (1/V) sum_{n != 0} delta(n) e^{ik.x} (Hermitian
+    spectrum, mean removed), dbar_i its mean over cube i, P^(l)_i the
+    power-spectrum multipoles of the cube's field taken as periodic (its own
+    transform (V_s/n_s^3) sum_x delta_x e^{-ik.x}, no window correction), on
+    the same shells in units of the parent's k_f (a cube mode n_s has
+    |n| = m |n_s|).  Returns dict(iB [n_ell][n_shells], Nk per cube, dbar)."""
+    assert n % m == 0
+    ns = n // m
+    V = float(box) ** 3
+    Vs = V / m ** 3
+    full = full_from_half(delta_half, n)
+    full[0, 0, 0] = 0.0
+    dx = np.real(np.fft.ifftn(full)) * (n ** 3 / V)
+    mu = mu_grid(ns)
+    n2s = n2_grid(ns).astype(np.float64) * m * m
+    e = [float(v) for v in edges]
+    masks = [(n2s > 0) & (n2s >= e[a] * e[a]) & (n2s < e[a + 1] * e[a + 1]) for a in range(len(e) - 1)]
+    Nk = np.array([float(mk.sum()) for mk in masks])
+    iB = np.zeros((len(ells), len(masks)))
+    dbar = np.zeros(m ** 3)
+    for c in range(m ** 3):
+        i, j, k = c // (m * m), (c // m) % m, c % m
+        sub = dx[i * ns:(i + 1) * ns, j * ns:(j + 1) * ns, k * ns:(k + 1) * ns]
+        dbar[c] = float(sub.mean())
+        pw = np.abs(np.fft.fftn(sub) * (Vs / ns ** 3)) ** 2
+        for a, mk in enumerate(masks):
+            if Nk[a] == 0:
+                continue
+            for li, ell in enumerate(ells):
+                iB[li, a] += dbar[c] * float(np.sum(legendre_weight(ell, mu[mk]) * pw[mk])) / (Vs * Nk[a])
+    return dict(iB=iB / m ** 3, Nk=Nk, dbar=dbar)

@@ -584,3 +584,118 @@ def test_skew_sign_follows_the_quadratic_term(ora):
         dk, _ = make_field(FieldModel(n=32, box=1000.0, quad=quad, f=0.0, sigma_g=0.3), 77, dtype=np.complex128)
         out.append(ora.skew_spectrum(dk, 32, 1000.0, [1, 5, 9], ells=(0,))["S"][0])
     assert np.all(out[0] > 0) and np.all(out[1] < 0)
+
+
+# ----------------------------------------------------------------------------
+# Integrated bispectrum (Sec. 3.4)
+# ----------------------------------------------------------------------------
+
+def _cube_field(n, m, c, s, wave):
+    """delta_x = c_i + s_i cos(2 pi q u / ns) on cube i, u the local coordinate
+    along axis `wave[0]` with q = wave[1]."""
+    ns = n // m
+    ax, q = wave
+    u = np.arange(ns)
+    prof = np.cos(2 * np.pi * q * u / ns)
+    shape = [1, 1, 1]
+    shape[ax] = ns
+    prof = prof.reshape(shape) * np.ones((ns, ns, ns))
+    x = np.zeros((n, n, n))
+    for i in range(m ** 3):
+        a, b, d = i // (m * m), (i // m) % m, i % m
+        x[a * ns:(a + 1) * ns, b * ns:(b + 1) * ns, d * ns:(d + 1) * ns] = c[i] + s[i] * prof
+    return x
+
+
+def _sub_counts(ns, m, edges):
+    """Modes of the ns^3 sub-grid per shell, the shell decided on m^2 |n_s|^2
+    (the sub-grid's fundamental is m parent fundamentals), by explicit loops."""
+    cnt = [0] * (len(edges) - 1)
+    fr = [j if j < ns // 2 else j - ns for j in range(ns)]
+    for fx in fr:
+        for fy in fr:
+            for fz in fr:
+                q = (fx * fx + fy * fy + fz * fz) * m * m
+                for a in range(len(edges) - 1):
+                    if q > 0 and edges[a] ** 2 <= q < edges[a + 1] ** 2:
+                        cnt[a] += 1
+    return np.array(cnt, dtype=np.float64)
+
+
+@pytest.mark.parametrize("ax,w", [(2, (1.0, 5.0, 9.0)), (0, (1.0, -2.5, 3.375))])
+def test_ib_plane_wave_closed_form(ora, ax, w):
+    # per cube: mean c_i and a cosine of amplitude s_i (mu = 1 along z, 0
+    # along x).  P^l_i holds the two modes +-q of |delta_s|^2 = (V_s s_i/2)^2,
+    # so iB^l = mean_i(c_i s_i^2) w_l V_s / (2 N_a) in the shell of |n| = m q
+    n, m, box, q = 16, 2, 500.0, 2
+    rng = np.random.default_rng(11)
+    c = rng.standard_normal(m ** 3) * 0.1
+    c -= c.mean()
+    s = 0.5 + rng.random(m ** 3)
+    x = _cube_field(n, m, c, s, (ax, q))
+    dk = delta_k_from_real(x, box)
+    edges = [1.0, 3.0, 5.0, 7.0, 9.0]
+    r = ora.integrated_bispectrum(dk, n, box, edges, m)
+    Vs = box ** 3 / m ** 3
+    Nk = _sub_counts(n // m, m, edges)
+    np.testing.assert_allclose(r["Nk"], Nk)
+    np.testing.assert_allclose(r["dbar"], c, atol=1e-13)
+    a = 1   # |n| = m q = 4 lies in shell 1, [3, 5)
+    want = np.zeros((3, len(edges) - 1))
+    for li in range(3):
+        want[li, a] = np.mean(c * s * s) * w[li] * Vs / (2 * Nk[a])
+    scale = np.max(np.abs(want))
+    np.testing.assert_allclose(r["iB"], want, atol=1e-12 * scale)
+
+
+def test_ib_brute_force_loops(ora):
+    # 4^3 grid in 2^3 cubes of side 2: sub-cube transforms and shell sums by
+    # explicit loops over cubes, points and modes
+    n, m, box = 4, 2, 10.0
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((n, n, n))
+    x -= x.mean()
+    dk = delta_k_from_real(x, box)
+    edges = [1.0, 2.5, 3.5, 5.0]
+    ells = (0, 2, 4)
+    ns, Vs = n // m, box ** 3 / m ** 3
+    fr = [j if j < ns // 2 else j - ns for j in range(ns)]
+    want = np.zeros((3, len(edges) - 1))
+    cnt = np.zeros(len(edges) - 1)
+    for i in range(m ** 3):
+        a0, b0, d0 = (i // (m * m)) * ns, ((i // m) % m) * ns, (i % m) * ns
+        dbar = sum(x[a0 + u, b0 + v, d0 + t] for u in range(ns) for v in range(ns) for t in range(ns)) / ns ** 3
+        for kx in range(ns):
+            for ky in range(ns):
+                for kz in range(ns):
+                    f = (fr[kx], fr[ky], fr[kz])
+                    q = (f[0] ** 2 + f[1] ** 2 + f[2] ** 2) * m * m
+                    sh = [a for a in range(len(edges) - 1) if q > 0 and edges[a] ** 2 <= q < edges[a + 1] ** 2]
+                    if not sh:
+                        continue
+                    acc = 0j
+                    for u in range(ns):
+                        for v in range(ns):
+                            for t in range(ns):
+                                ph = -2j * math.pi * (kx * u + ky * v + kz * t) / ns
+                                acc += x[a0 + u, b0 + v, d0 + t] * complex(math.cos(ph.imag), math.sin(ph.imag))
+                    d = acc * Vs / ns ** 3
+                    mu = f[2] * m / math.sqrt(q)
+                    for li, ell in enumerate(ells):
+                        leg = {0: 1.0, 2: 0.5 * (3 * mu * mu - 1), 4: (35 * mu ** 4 - 30 * mu * mu + 3) / 8}[ell]
+                        want[li, sh[0]] += dbar * (2 * ell + 1) * leg * abs(d) ** 2 / Vs
+                    if i == 0:
+                        cnt[sh[0]] += 1
+    want /= np.where(cnt > 0, cnt, 1)[None, :] * m ** 3
+    r = ora.integrated_bispectrum(dk, n, box, edges, m)
+    np.testing.assert_allclose(r["Nk"], cnt)
+    np.testing.assert_allclose(r["iB"], want, rtol=1e-10, atol=1e-12 * np.max(np.abs(want)))
+
+
+def test_ib_single_cube_vanishes(ora):
+    # m = 1: the one sub-volume is the whole box, whose mean (the n = 0 mode)
+    # is not part of delta, so every product P dbar is zero
+    dk, _ = make_field(FieldModel(n=16, box=300.0, sigma_g=0.3), 2, dtype=np.complex128)
+    r = ora.integrated_bispectrum(dk, 16, 300.0, [1.0, 3.0, 5.0, 7.0], 1)
+    assert abs(r["dbar"][0]) < 1e-12
+    assert np.max(np.abs(r["iB"])) < 1e-12 * max(1.0, np.max(np.abs(ora.power_multipoles(dk, 16, 300.0, [1.0, 3.0, 5.0, 7.0])["P"])))
