@@ -281,6 +281,21 @@ def main():
     torch.cuda.synchronize()
     sk_ms = s0.elapsed_time(s1) / 5
     del sws
+    # integrated-bispectrum multipoles (Sec. 3.4) on the same shells over 8^3
+    # sub-cubes: inverse FFT of delta, 512 batched sub-cube forward FFTs,
+    # cube-mean-weighted shell sums (separate workspace)
+    ib_m = 8 if args.n % 8 == 0 and args.n // 8 >= 8 else 2
+    bsp.load().bsp_ib_workspace_size(est.plan, ib_m, _ct.byref(_sb))
+    iws = torch.empty(_sb.value, dtype=torch.uint8, device="cuda")
+    est.integrated(d, ib_m, ws=iws)
+    torch.cuda.synchronize()
+    s0.record(stream)
+    for _ in range(5):
+        est.integrated(d, ib_m, ws=iws)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ib_ms = s0.elapsed_time(s1) / 5
+    del iws
     # density input stage (CIC + interlacing + forward FFT) on the particle workload's
     # shape: 256^3 grid, 4 Mi particles (uniform positions: the cost does not depend on them)
     dn, dnp = 256, 4 * 2 ** 20
@@ -386,6 +401,8 @@ def main():
                               "achieved_gbs": den_bytes / (den_ms / 1e3) / 1e9,
                               "frac_hbm": den_bytes / (den_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
             "skew_spectrum": {"ms": sk_ms, "shells_per_s": args.shells * 3 / (sk_ms / 1e3)},
+            "integrated_bispectrum": {"ms": ib_ms, "subcubes": ib_m ** 3, "subcube_side": args.n // ib_m,
+                                      "shells_per_s": args.shells * 3 / (ib_ms / 1e3)},
             "power_multipoles": {"ms": pw_ms, "shells_per_s": args.shells * 3 / (pw_ms / 1e3),
                                  "algorithmic_bytes": pw_bytes, "achieved_gbs": pw_bytes / (pw_ms / 1e3) / 1e9,
                                  "frac_hbm": pw_bytes / (pw_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}}

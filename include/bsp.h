@@ -309,6 +309,34 @@ bsp_status bsp_skew_workspace_size(const bsp_plan* plan, size_t* bytes);
 bsp_status bsp_skew_compute(bsp_plan* plan, const void* delta_k, void* ws, size_t ws_bytes, void* stream, double* S,
                             double* Nk);
 
+/*
+ * Integrated-bispectrum multipoles on the plan's shells (Sec. 3.4, the
+ * estimator after Eq. iB_expectation, with P^(l) for the multipoles):
+ *   iB^l_a = (1/N_s) sum_{i=1}^{N_s} P^l_a,i dbar_i,
+ * the box cut into N_s = m^3 cubes of side n/m cells (cube i = (i_x m + i_y) m
+ * + i_z, offset (i_x, i_y, i_z) n/m cells), delta(x) the field of every mode
+ * of delta_k but the mean, dbar_i its mean over cube i, and P^l_a,i the
+ * power-spectrum multipoles of the cube's field taken as periodic (its own
+ * transform, V_s = V/m^3, no window correction) on the plan's shells, whose
+ * edges stay in units of the whole box's k_f (a cube mode n_s sits at
+ * |n| = m |n_s|; shells holding no such mode give iB = 0 and Nk = 0).
+ *   delta_k: device complex64 [n][n][n/2+1].
+ *   m:       cubes per side, 1 <= m, n % m == 0, side s = n/m even, >= 8 and
+ *            of the form 2^a 3^b 5^c (s/2 too), m^3 <= 65535 (EINVAL /
+ *            EUNSUPPORTED otherwise).
+ *   ws:      device workspace of bsp_ib_workspace_size bytes (~12 n^3),
+ *            256-byte aligned, separate from the plan's; ws_bytes its size
+ *            (ENOMEM if smaller).
+ *   iB:      device FP64 [n_ell][n_shells] (out); Nk: device FP64 [n_shells]
+ *            modes per cube in each shell (out), or NULL.
+ * Asynchronous on `stream`; deterministic.  Standard plans only.  The first
+ * call with a given m uploads the sub-grid's shell table (a synchronous
+ * allocation; not inside a graph capture).
+ */
+bsp_status bsp_ib_workspace_size(const bsp_plan* plan, int m, size_t* bytes);
+bsp_status bsp_ib_compute(bsp_plan* plan, const void* delta_k, int m, void* ws, size_t ws_bytes, void* stream,
+                          double* iB, double* Nk);
+
 /* Raw sums T^l = sum_x F^l_a F_b F_c of the last bsp_compute (FP64
  * [n_ell][n_bins], device), copied into T (device).  For tests. */
 bsp_status bsp_last_raw(const bsp_plan* plan, void* ws, void* stream, double* T);

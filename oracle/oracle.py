@@ -679,7 +679,9 @@ def integrated_bispectrum(delta_half: np.ndarray, n: int, box: float, edges, m: 
     power-spectrum multipoles of the cube's field taken as periodic (its own
     transform (V_s/n_s^3) sum_x delta_x e^{-ik.x}, no window correction), on
     the same shells in units of the parent's k_f (a cube mode n_s has
-    |n| = m |n_s|).  Returns dict(iB [n_ell][n_shells], Nk per cube, dbar)."""
+    |n| = m |n_s|).  Returns dict(iB [n_ell][n_shells], Nk per cube, dbar,
+    absum = (1/N_s) sum_i |dbar_i| (1/(V_s N_a)) sum_n |w_l| |delta_s|^2, the
+    size of the products the sum adds up and partly cancels)."""
     assert n % m == 0
     ns = n // m
     V = float(box) ** 3
@@ -693,6 +695,7 @@ def integrated_bispectrum(delta_half: np.ndarray, n: int, box: float, edges, m: 
     masks = [(n2s > 0) & (n2s >= e[a] * e[a]) & (n2s < e[a + 1] * e[a + 1]) for a in range(len(e) - 1)]
     Nk = np.array([float(mk.sum()) for mk in masks])
     iB = np.zeros((len(ells), len(masks)))
+    absum = np.zeros((len(ells), len(masks)))
     dbar = np.zeros(m ** 3)
     for c in range(m ** 3):
         i, j, k = c // (m * m), (c // m) % m, c % m
@@ -703,5 +706,7 @@ def integrated_bispectrum(delta_half: np.ndarray, n: int, box: float, edges, m: 
             if Nk[a] == 0:
                 continue
             for li, ell in enumerate(ells):
-                iB[li, a] += dbar[c] * float(np.sum(legendre_weight(ell, mu[mk]) * pw[mk])) / (Vs * Nk[a])
-    return dict(iB=iB / m ** 3, Nk=Nk, dbar=dbar)
+                w = legendre_weight(ell, mu[mk])
+                iB[li, a] += dbar[c] * float(np.sum(w * pw[mk])) / (Vs * Nk[a])
+                absum[li, a] += abs(dbar[c]) * float(np.sum(np.abs(w) * pw[mk])) / (Vs * Nk[a])
+    return dict(iB=iB / m ** 3, Nk=Nk, dbar=dbar, absum=absum / m ** 3)

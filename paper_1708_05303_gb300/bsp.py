@@ -52,6 +52,8 @@ _SIGS = [
     ("bsp_density_workspace_size", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("bsp_skew_workspace_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("bsp_skew_compute", ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
+    ("bsp_ib_workspace_size", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    ("bsp_ib_compute", ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_size_t, _P, _P, _P]),
     ("bsp_density_cic", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_longlong, _P, _P, ctypes.c_size_t, _P,
                                        _P, ctypes.POINTER(ctypes.c_double)]),
     ("bsp_device_status", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
@@ -477,6 +479,23 @@ class Bispectrum:
         _check(load().bsp_skew_compute(self.plan, _dptr(delta_k), _dptr(ws), int(ws.numel()), _stream_handle(stream),
                                        _dptr(S), _dptr(Nk)), "bsp_skew_compute")
         return S, Nk
+
+    def integrated(self, delta_k, m, ws=None, stream=None):
+        """Integrated-bispectrum multipoles iB [n_ell][n_shells] over m^3
+        sub-cubes and the per-cube mode counts Nk (FP64, device) on the plan's
+        shells; ``ws`` an optional reusable uint8 CUDA tensor of
+        bsp_ib_workspace_size bytes."""
+        import torch
+
+        nb = ctypes.c_size_t()
+        _check(load().bsp_ib_workspace_size(self.plan, int(m), ctypes.byref(nb)), "bsp_ib_workspace_size")
+        if ws is None or ws.numel() < nb.value:
+            ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+        iB = torch.empty((len(self.ells), len(self.edges) - 1), dtype=torch.float64, device="cuda")
+        Nk = torch.empty(len(self.edges) - 1, dtype=torch.float64, device="cuda")
+        _check(load().bsp_ib_compute(self.plan, _dptr(delta_k), int(m), _dptr(ws), int(ws.numel()),
+                                     _stream_handle(stream), _dptr(iB), _dptr(Nk)), "bsp_ib_compute")
+        return iB, Nk
 
     def raw(self, stream=None):
         import torch

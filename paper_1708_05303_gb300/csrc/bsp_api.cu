@@ -336,6 +336,8 @@ struct bsp_plan {
     int fb_cap = 1;                   // FFT batch width the workspace was sized for
     int16_t* d_shell_of = nullptr;
     FieldDesc* d_fd_raw = nullptr;    // one field: delta on every mode but the mean (skew spectrum)
+    int ib_m = 0;                     // integrated bispectrum: cubes per side of the cached shell table
+    int16_t* d_shell_sub = nullptr;   // shell of each |n_s|^2 of the sub-cube grid (|n| = m |n_s|)
     cx<float>* d_tw32 = nullptr;
     cx<double>* d_tw64 = nullptr;
     FieldDesc* d_fd_delta = nullptr;  // [nslot*nsh], or [3][nslot*nsh] with shot noise
@@ -393,7 +395,7 @@ struct bsp_plan {
 
     ~bsp_plan() {
         for (auto e : ev_pool) cudaEventDestroy(e);
-        cudaFree(d_shell_of); cudaFree(d_tw32); cudaFree(d_tw64); cudaFree(d_fd_raw);
+        cudaFree(d_shell_of); cudaFree(d_tw32); cudaFree(d_tw64); cudaFree(d_fd_raw); cudaFree(d_shell_sub);
         cudaFree(d_fd_delta); cudaFree(d_fd_unit); cudaFree(d_counts);
         cudaFree(d_fd_tc); cudaFree(d_tc_works); cudaFree(d_tc_pairs); cudaFree(d_tc_loc); cudaFree(d_err);
         cudaFree(d_fmax);
@@ -1354,6 +1356,108 @@ bsp_status bsp_skew_compute(bsp_plan* p, const void* delta_k, void* ws, size_t w
     e = launch_power((const cx<float>*)delta_k, t1, V / (double)n3, p->geom, p->d_shell_of, p->nsh, pe, V, 0.0,
                      nblocks, (double*)t2, S, Nk, st);
     if (e != cudaSuccess) return cuda_fail(e, "skew (shell sums)");
+    return BSP_OK;
+}
+
+// Integrated bispectrum (Sec. 3.4).  Workspace: the real field x [n^3] FP32,
+// then one region used first by the inverse FFT's two half spectra and then
+// by the m^3 sub-cube spectra, their twiddles and the per-CTA sums.
+struct IbLayout {
+    size_t t1, t2, sub, tw, part, end;
+    int nbx;   // CTAs per cube of the shell sums
+};
+
+static bool ib_geom(const bsp_plan* p, int m, FftGeom* gs) {
+    if (m < 1 || p->n % m != 0) return false;
+    const int s = p->n / m;
+    if (!density_geom(s, gs)) return false;
+    // only |n_s| with m^2 |n_s|^2 below the top edge lie in a shell
+    const double emax = p->edges.back();
+    int K = 0;
+    while ((double)(K + 1) * (K + 1) * m * m < emax * emax) ++K;
+    if (K < s / 2) {
+        gs->K = K;
+        gs->nK = 2 * K + 1;
+        gs->pruned = 1;
+        gs->nKz = K + 1;
+    }
+    return true;
+}
+
+static IbLayout ib_layout(const bsp_plan* p, int m, const FftGeom& gs) {
+    const int n = p->n, s = n / m, nc = m * m * m;
+    IbLayout L{};
+    const size_t x = round256((size_t)n * n * n * sizeof(float));
+    const size_t h = round256((size_t)n * n * (n / 2 + 1) * sizeof(cx<float>));
+    L.t1 = x;
+    L.t2 = x + h;
+    L.sub = x;
+    L.tw = L.sub + round256((size_t)nc * s * s * (s / 2 + 1) * sizeof(cx<float>));
+    L.part = L.tw + round256((size_t)s * sizeof(cx<float>));
+    const long long rows = (long long)gs.nK * gs.nK;
+    L.nbx = (int)std::max<long long>(1, std::min<long long>(rows / 8, (4LL * p->nsm + nc - 1) / nc));
+    const size_t part = round256(power_partial_bytes(L.nbx * nc, p->nsh, (int)p->ells.size()));
+    L.end = std::max(x + 2 * h, L.part + part);
+    return L;
+}
+
+bsp_status bsp_ib_workspace_size(const bsp_plan* p, int m, size_t* bytes) {
+    FftGeom gs;
+    if (!p || !bytes || p->modal || !ib_geom(p, m, &gs) || m * m * m > 65535) return BSP_EINVAL;
+    *bytes = ib_layout(p, m, gs).end;
+    return BSP_OK;
+}
+
+bsp_status bsp_ib_compute(bsp_plan* p, const void* delta_k, int m, void* ws, size_t ws_bytes, void* stream,
+                          double* iB, double* Nk) {
+    if (!p || !delta_k || !ws || !iB || !aligned256(ws)) return BSP_EINVAL;
+    if (p->modal || p->nsh <= 0 || p->ells.size() > 3 || !p->d_fd_raw || m < 1 || m * m * m > 65535)
+        return BSP_EINVAL;
+    FftGeom full, gs;
+    if (!density_geom(p->n, &full)) return BSP_EUNSUPPORTED;
+    if (!ib_geom(p, m, &gs)) return BSP_EUNSUPPORTED;
+    const IbLayout L = ib_layout(p, m, gs);
+    if (ws_bytes < L.end) return BSP_ENOMEM;
+    if (p->ib_m != m) {   // shell table of the sub-cube grid, built once per m
+        std::vector<int16_t> tab(gs.n2max + 1, -1);
+        for (int q = 1; q <= gs.n2max; ++q) {
+            const double n2 = (double)q * m * m;
+            for (int a = 0; a < p->nsh; ++a)
+                if (n2 >= p->edges[a] * p->edges[a] && n2 < p->edges[a + 1] * p->edges[a + 1]) {
+                    tab[q] = (int16_t)a;
+                    break;
+                }
+        }
+        cudaFree(p->d_shell_sub);
+        p->d_shell_sub = nullptr;
+        p->ib_m = 0;
+        bsp_status st = upload(&p->d_shell_sub, tab);
+        if (st != BSP_OK) return st;
+        p->ib_m = m;
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    float* x = (float*)base;
+    const int n = p->n, s = n / m, nc = m * m * m;
+    // x = sum_{n != 0} delta(n) e^{ik.x} = V delta(x)
+    cudaError_t e = launch_fft_fields<float>(full, (const cx<float>*)delta_k, p->d_shell_of, nullptr, p->d_fd_raw, 1,
+                                             p->d_tw32, (cx<float>*)(base + L.t1), (cx<float>*)(base + L.t2), x,
+                                             (size_t)n * n * n, nullptr, nullptr, 0, nullptr, nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "integrated bispectrum (inverse FFT)");
+    // T_c = (1/(V s^3)) sum_{x in c} x e^{-ik.x}: T_c(0) is the cube mean of
+    // delta, and the cube's own transform is delta_c(k) = V_s T_c(k)
+    const double V = p->box * p->box * p->box, Vs = V / (double)nc;
+    cx<float>* T = (cx<float>*)(base + L.sub);
+    e = launch_forward_subcubes(gs, n, m, x, (float)(1.0 / (V * (double)s * s * s)), (cx<float>*)(base + L.tw), T, st);
+    if (e != cudaSuccess) return cuda_fail(e, "integrated bispectrum (sub-cube FFTs)");
+    PowerEll pe{};
+    pe.n = (int)p->ells.size();
+    for (int i = 0; i < pe.n; ++i) pe.ell[i] = p->ells[i];
+    // iB^l_a = (1/m^3) sum_c T_c(0) (V_s^2 / (V_s N_a)) sum_{n in a} w_l |T_c|^2
+    //        = V_s (sum_c T_c(0) sum w_l |T_c|^2) / (m^3 N_a)
+    e = launch_power(T, nullptr, Vs, gs, p->d_shell_sub, p->nsh, pe, 1.0, 0.0, L.nbx, (double*)(base + L.part), iB,
+                     Nk, st, nc, (size_t)s * s * (s / 2 + 1), 1);
+    if (e != cudaSuccess) return cuda_fail(e, "integrated bispectrum (shell sums)");
     return BSP_OK;
 }
 

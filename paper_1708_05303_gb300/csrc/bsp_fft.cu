@@ -622,14 +622,16 @@ __global__ void k_twiddles(int n, cx<float>* __restrict__ tw) {
     tw[t] = cx<float>{(float)c, (float)s};
 }
 
-// z pass: P real lines (x fixed, y0 .. y0 + P - 1) of grid blockIdx.y, with
+// z pass: P real lines (x fixed, y0 .. y0 + P - 1) of grid blockIdx.y (or,
+// with msub > 0, of the sub-cube blockIdx.y of side n of a grid of side
+// nfull cut into msub^3 cubes), with
 // delta = a g + b applied on load, packed as z_m = d_{2m} + i d_{2m+1}; an
 // M = n/2-point FFT gives Z; X_k = E_k + e^{-2 pi i k/n} O_k with
 // E_k = (Z_k + conj Z_{M-k})/2, O_k = (Z_k - conj Z_{M-k})/(2i), k = 0 .. M.
 template <int P, int NN, bool SQ = false>
 __global__ void __launch_bounds__(NTHR) k_fwd_z(FftGeom g, const float* __restrict__ grid, size_t gstride, float a,
                                                 float b, const cx<float>* __restrict__ twg, cx<float>* __restrict__ T,
-                                                size_t tstride) {
+                                                size_t tstride, int msub = 0, int nfull = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = NN ? NN : g.n, M = N / 2, H = M + 1;
     cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
@@ -638,12 +640,19 @@ __global__ void __launch_bounds__(NTHR) k_fwd_z(FftGeom g, const float* __restri
     const int nyb = (N + P - 1) / P;
     const int x = blockIdx.x / nyb, y0 = (blockIdx.x % nyb) * P;
     const float* src = grid + (size_t)blockIdx.y * gstride;
+    size_t sx = (size_t)N * N, sy = (size_t)N;   // element strides of x and y in the source
+    if (msub > 0) {
+        const int c = blockIdx.y, cx_ = c / (msub * msub), cy = (c / msub) % msub, cz = c % msub;
+        sx = (size_t)nfull * nfull;
+        sy = (size_t)nfull;
+        src = grid + (size_t)cx_ * N * sx + (size_t)cy * N * sy + (size_t)cz * N;
+    }
     for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
     for (int e = threadIdx.x; e < M * P; e += NTHR) {
         const int m = e % M, p = e / M, y = y0 + p;
         cx<float> v = {0.f, 0.f};
         if (y < N) {
-            const float2 r = *reinterpret_cast<const float2*>(src + ((size_t)x * N + y) * N + 2 * m);
+            const float2 r = *reinterpret_cast<const float2*>(src + (size_t)x * sx + (size_t)y * sy + 2 * m);
             const float r0 = SQ ? r.x * r.x : r.x, r1 = SQ ? r.y * r.y : r.y;
             v = cx<float>{a * r0 + b, -(a * r1 + b)};   // conjugated
         }
@@ -851,6 +860,46 @@ cudaError_t launch_forward_square(const FftGeom& g, const float* x, float a, con
         case 256: return launch_forward_square_n<256>(g, x, a, tw, T, st);
         case 512: return launch_forward_square_n<512>(g, x, a, tw, T, st);
         default: return launch_forward_square_n<0>(g, x, a, tw, T, st);
+    }
+}
+
+template <int NN>
+cudaError_t launch_forward_subcubes_n(const FftGeom& g, int nfull, int m, const float* x, float a, cx<float>* tw,
+                                      cx<float>* T, cudaStream_t st) {
+    constexpr int P = 8;
+    const int N = g.n, M = N / 2, H = M + 1, nc = m * m * m;
+    const size_t smz = sizeof(cx<float>) * ((size_t)N + 2 * (size_t)smem_elems<false, P>(M));
+    const size_t sma = sizeof(cx<float>) * ((size_t)N + 2 * (size_t)smem_elems<true, P>(N));
+    static size_t setz = 0, seta = 0;   // raised once per size, never inside a graph capture
+    cudaError_t e;
+    if (smz > setz) {
+        if ((e = cudaFuncSetAttribute(k_fwd_z<P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz)) !=
+            cudaSuccess)
+            return e;
+        setz = smz;
+    }
+    if (sma > seta) {
+        if ((e = cudaFuncSetAttribute(k_fwd_axis<P, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma)) !=
+            cudaSuccess)
+            return e;
+        seta = sma;
+    }
+    const size_t tstride = (size_t)N * N * H;
+    k_twiddles<<<(N + 255) / 256, 256, 0, st>>>(N, tw);
+    k_fwd_z<P, NN><<<dim3(N * ((N + P - 1) / P), nc), NTHR, smz, st>>>(g, x, 0, a, 0.f, tw, T, tstride, m, nfull);
+    const int nkzb = (H + P - 1) / P;
+    k_fwd_axis<P, NN><<<dim3(N * nkzb, nc), NTHR, sma, st>>>(g, tw, T, tstride, (size_t)N * H, (size_t)H);
+    k_fwd_axis<P, NN><<<dim3(N * nkzb, nc), NTHR, sma, st>>>(g, tw, T, tstride, (size_t)H, (size_t)N * H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_subcubes(const FftGeom& g, int nfull, int m, const float* x, float a, cx<float>* tw,
+                                    cx<float>* T, cudaStream_t st) {
+    if (m < 1 || m * g.n != nfull || m * m * m > 65535) return cudaErrorInvalidValue;
+    switch (g.n) {
+        case 64: return launch_forward_subcubes_n<64>(g, nfull, m, x, a, tw, T, st);
+        case 128: return launch_forward_subcubes_n<128>(g, nfull, m, x, a, tw, T, st);
+        default: return launch_forward_subcubes_n<0>(g, nfull, m, x, a, tw, T, st);
     }
 }
 

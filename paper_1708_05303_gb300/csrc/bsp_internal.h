@@ -152,6 +152,12 @@ cudaError_t launch_density(const FftGeom& g, const float* pos, long long np, dou
 // field x [n][n][n]; spectrum T [n][n][n/2+1]; tw = exp(+2 pi i t/n), t < n.
 cudaError_t launch_forward_square(const FftGeom& g, const float* x, float a, const cx<float>* tw, cx<float>* T,
                                   cudaStream_t st);
+// Forward real-to-complex FFTs of the m^3 sub-cubes of side s = n/m of a real
+// field x [n][n][n] (g: the geometry of side s), each scaled by a:
+// T [m^3][s][s][s/2+1], cube c = (c_x m + c_y) m + c_z at x offset (c_x s,
+// c_y s, c_z s); tw (workspace, s entries) receives exp(+2 pi i t/s).
+cudaError_t launch_forward_subcubes(const FftGeom& g, int nfull, int m, const float* x, float a, cx<float>* tw,
+                                    cx<float>* T, cudaStream_t st);
 
 // ---- launchers (bsp_power.cu) ----
 struct PowerEll {   // the multipoles of a power-spectrum call (even l in {0, 2, 4})
@@ -161,9 +167,14 @@ struct PowerEll {   // the multipoles of a power-spectrum call (even l in {0, 2,
 size_t power_partial_bytes(int nblocks, int nsh, int nell);
 // P^l_a (Q == nullptr: w_l |delta|^2) or the cross spectrum (w_l Re conj(Q) delta,
 // Q in the half-spectrum layout of delta, multiplied by num_scale), over V N_a.
+// With nbatch > 1, delta holds nbatch spectra bstride elements apart, each
+// summed by nblocks CTAs (partial: nbatch * nblocks slots); with dc_weight
+// every product of spectrum b is multiplied by Re delta_b(0), and Nk is the
+// count per spectrum.
 cudaError_t launch_power(const cx<float>* delta, const cx<float>* Q, double num_scale, const FftGeom& g,
                          const int16_t* shell_of, int nsh, const PowerEll& ells, double V, double nbar, int nblocks,
-                         double* partial, double* P, double* Nk, cudaStream_t st);
+                         double* partial, double* P, double* Nk, cudaStream_t st, int nbatch = 1,
+                         size_t bstride = 0, int dc_weight = 0);
 
 // ---- launchers (bsp_modal.cu) ----
 cudaError_t launch_modal_assemble(const double* T, const double* U, const int* ells, int n_ell, int nf,

@@ -11,17 +11,24 @@
 // One pass: the products w_l |delta|^2 are formed in FP32 (the input is
 // FP32; GB300's FP64 rate is a small fraction of its FP32 rate), summed in
 // FP64 per warp and shell, per CTA, then over CTAs in a fixed order by a
-// second kernel (deterministic), which normalises.
+// second kernel (deterministic), which normalises.  A batch of spectra (the
+// sub-cubes of the integrated bispectrum, Sec. 3.4) runs as gridDim.y, each
+// spectrum's products optionally weighted by its own Re delta(0).
 #include "bsp_internal.h"
 
 namespace bsp {
 
 namespace {
 
-__device__ __forceinline__ float legendre_w(int ell, float mu2) {
+// w_l = (2l+1) L_l(mu), mu^2 = fz2/n2, from the exact integer numerators
+// 3 fz2 - n2 and 35 fz2^2 - 30 fz2 n2 + 3 n2^2: a few ulp of w_l itself (not
+// of 2l+1), and exactly 0 where L_l vanishes on the lattice (mu^2 = 1/3).
+__device__ __forceinline__ float legendre_w(int ell, int fz2, int n2) {
     if (ell == 0) return 1.f;
-    if (ell == 2) return 2.5f * (3.f * mu2 - 1.f);                             // 5 L_2
-    return 1.125f * ((35.f * mu2 - 30.f) * mu2 + 3.f);                         // 9 L_4
+    if (ell == 2) return 2.5f * (float)(3 * fz2 - n2) / (float)n2;             // 5 L_2
+    const long long f = fz2, q = n2;
+    const float d = (float)n2;
+    return 1.125f * (float)(35 * f * f - 30 * f * q + 3 * q * q) / (d * d);    // 9 L_4
 }
 
 constexpr int PW_WARPS = 8;   // warps per CTA
@@ -29,7 +36,8 @@ constexpr int PW_WARPS = 8;   // warps per CTA
 __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>* __restrict__ delta,
                                                                  const cx<float>* __restrict__ Q, FftGeom g,
                                                                  const int16_t* __restrict__ shell_of, int nsh,
-                                                                 PowerEll ells, double* __restrict__ partial) {
+                                                                 PowerEll ells, double* __restrict__ partial,
+                                                                 size_t bstride, int dc_weight) {
     // per warp [2 nell + 1][nsh] FP64: sum w|d|^2 per l, sum w per l, mode count
     extern __shared__ double acc[];
     const int nell = ells.n, per = (2 * nell + 1) * nsh;
@@ -38,6 +46,10 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
     const int N = g.n, H = N / 2 + 1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double* mine = acc + (size_t)wid * per;
+    // spectrum blockIdx.y of a batch; with dc_weight its products carry the
+    // factor Re delta(0) of that spectrum (the cube mean of Sec. 3.4)
+    delta += (size_t)blockIdx.y * bstride;
+    const float dcw = dc_weight ? delta[0].re : 1.f;
     const long long rows = (long long)g.nK * g.nK;
     // one warp per row, 32 consecutive n_z at a time: along a row |n| grows with
     // n_z, so the lanes of one shell are a contiguous run; a segmented sum over
@@ -80,10 +92,9 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
                         }
                         p = qr * re + qi * im;
                     }
-                    p *= h;
-                    const float mu2 = (float)(fz * fz) / (float)n2;
+                    p *= h * dcw;
                     for (int l = 0; l < nell; ++l) {
-                        const float w = legendre_w(ells.ell[l], mu2);
+                        const float w = legendre_w(ells.ell[l], fz * fz, n2);
                         v[l] = w * p;
                         v[3 + l] = w * h;
                     }
@@ -113,7 +124,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
         }
     }
     __syncthreads();
-    double* dst = partial + (size_t)blockIdx.x * per;
+    double* dst = partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * per;
     for (int i = threadIdx.x; i < per; i += blockDim.x) {
         double t = 0.0;
         for (int w = 0; w < PW_WARPS; ++w) t += acc[(size_t)w * per + i];   // fixed order
@@ -122,7 +133,8 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
 }
 
 __global__ void k_power_final(const double* __restrict__ partial, int nblocks, int nsh, int nell, double V,
-                              double nbar, double num_scale, double* __restrict__ P, double* __restrict__ Nk) {
+                              double nbar, double num_scale, int nbatch, double* __restrict__ P,
+                              double* __restrict__ Nk) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nell * nsh) return;
     const int l = t / nsh, s = t % nsh, per = (2 * nell + 1) * nsh;
@@ -139,7 +151,7 @@ __global__ void k_power_final(const double* __restrict__ partial, int nblocks, i
         if (nbar > 0.0) v -= sw / (nbar * sn);
     }
     P[t] = v;
-    if (Nk && l == 0) Nk[s] = sn;
+    if (Nk && l == 0) Nk[s] = sn / (double)nbatch;
 }
 
 }  // namespace
@@ -150,7 +162,8 @@ size_t power_partial_bytes(int nblocks, int nsh, int nell) {
 
 cudaError_t launch_power(const cx<float>* delta, const cx<float>* Q, double num_scale, const FftGeom& g,
                          const int16_t* shell_of, int nsh, const PowerEll& ells, double V, double nbar, int nblocks,
-                         double* partial, double* P, double* Nk, cudaStream_t st) {
+                         double* partial, double* P, double* Nk, cudaStream_t st, int nbatch, size_t bstride,
+                         int dc_weight) {
     const size_t smem = (size_t)PW_WARPS * (2 * ells.n + 1) * nsh * sizeof(double);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     static size_t set = 0;   // raised once per size, never inside a graph capture
@@ -161,9 +174,12 @@ cudaError_t launch_power(const cx<float>* delta, const cx<float>* Q, double num_
             return e;
         set = smem;
     }
-    k_power_partial<<<nblocks, 32 * PW_WARPS, smem, st>>>(delta, Q, g, shell_of, nsh, ells, partial);
+    if (nbatch < 1 || nbatch > 65535 || (nbatch > 1 && Q)) return cudaErrorInvalidValue;
+    k_power_partial<<<dim3(nblocks, nbatch), 32 * PW_WARPS, smem, st>>>(delta, Q, g, shell_of, nsh, ells, partial,
+                                                                        bstride, dc_weight);
     const int nt = ells.n * nsh;
-    k_power_final<<<(nt + 127) / 128, 128, 0, st>>>(partial, nblocks, nsh, ells.n, V, nbar, num_scale, P, Nk);
+    k_power_final<<<(nt + 127) / 128, 128, 0, st>>>(partial, nblocks * nbatch, nsh, ells.n, V, nbar, num_scale,
+                                                    nbatch, P, Nk);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,94 @@
+"""GPU integrated-bispectrum multipoles (Sec. 3.4) against the FP64 oracle on
+the same complex64 spectrum.  The GPU path is an FP32 inverse FFT of the whole
+box, FP32 forward FFTs of the m^3 sub-cubes, and FP32 products weighted by the
+cube means, summed in FP64.  iB is a signed sum over cubes and modes that
+cancels, so the gate is 1e-5 of the size of its products, (1/N_s) sum_i
+|dbar_i| (1/(V_s N_a)) sum_n |w_l| |delta_s|^2, or of that size's rms over
+shells where it is smaller (a shell of mu^2 = 1/3 modes only has w_2 = 0);
+the error is also reported against the rms of iB over shells.  Repeats are
+bit-identical."""
+import numpy as np
+import pytest
+
+from paper_1708_05303_gb300.synth import FieldModel, linear_edges, make_field
+
+pytestmark = pytest.mark.gpu
+BOX = 1000.0
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_05303_gb300 import build
+
+    build.build()
+    return torch
+
+
+def _check(torch, ora, n, nsh, width, m, seed, gate=1e-5):
+    from paper_1708_05303_gb300 import bsp
+
+    edges = linear_edges(nsh, width)
+    dk, _ = make_field(FieldModel(n=n, box=BOX, sigma_g=0.3), seed)
+    est = bsp.Bispectrum(n, BOX, edges, (0, 2, 4))
+    d = torch.from_numpy(dk).cuda()
+    iB, Nk = est.integrated(d, m)
+    g1 = iB.cpu().numpy().copy()
+    iB2, _ = est.integrated(d, m)
+    g2 = iB2.cpu().numpy()
+    nk = Nk.cpu().numpy()
+    est.close()
+    r = ora.integrated_bispectrum(dk.astype(np.complex128), n, BOX, edges, m)
+    assert np.array_equal(nk, r["Nk"])
+    assert np.array_equal(g1, g2)
+    live = r["Nk"] > 0
+    assert np.all(g1[:, ~live] == 0.0)
+    ts = r["absum"][:, live]
+    ts = np.maximum(ts, np.sqrt(np.mean(ts ** 2, axis=1, keepdims=True)))
+    e = float(np.max(np.abs(g1 - r["iB"])[:, live] / ts))
+    rms = np.sqrt(np.mean(r["iB"][:, live] ** 2, axis=1, keepdims=True))
+    e_rms = float(np.max(np.abs(g1 - r["iB"])[:, live] / np.maximum(np.abs(r["iB"][:, live]), rms)))
+    print("iB %d^3, %d shells, m=%d: %.3g of the term scale, %.3g of max(|iB|, rms)" % (n, nsh, m, e, e_rms))
+    assert e <= gate
+    return g1, r
+
+
+@pytest.mark.parametrize("n,nsh,width,m", [(64, 16, 2.0, 2), (64, 16, 2.0, 4), (48, 10, 2.0, 3),
+                                           (128, 20, 2.0, 2), (128, 40, 1.5, 8)])
+def test_ib_matches_oracle(torch_cuda, ora, n, nsh, width, m):
+    _check(torch_cuda, ora, n, nsh, width, m, 2017 + n + m)
+
+
+def test_ib_single_cube_is_zero(torch_cuda, ora):
+    # m = 1: the cube is the box, whose mean is not part of delta; the GPU's
+    # FP32 mean is rounding noise, a small fraction of the field's rms, so
+    # |iB^l| stays below 1e-5 sigma max(|P^l|, rms P^l)
+    from paper_1708_05303_gb300 import bsp
+
+    n, edges = 64, linear_edges(16, 2.0)
+    dk, _ = make_field(FieldModel(n=n, box=BOX, sigma_g=0.3), 99)
+    est = bsp.Bispectrum(n, BOX, edges, (0, 2, 4))
+    iB, Nk = est.integrated(torch_cuda.from_numpy(dk).cuda(), 1)
+    g = iB.cpu().numpy()
+    est.close()
+    _ib_single_cube_bound(ora, dk, n, edges, g, Nk.cpu().numpy())
+
+
+def _ib_single_cube_bound(ora, dk, n, edges, g, nk):
+    d = dk.astype(np.complex128)
+    pm = ora.power_multipoles(d, n, BOX, edges)
+    assert np.array_equal(nk, pm["Nk"])
+    full = ora.full_from_half(d, n)
+    full[0, 0, 0] = 0.0
+    sigma = float(np.sqrt(np.sum(np.abs(full) ** 2))) / BOX ** 3
+    P = pm["P"]
+    lim = 1e-5 * sigma * np.maximum(np.abs(P), np.sqrt(np.mean(P ** 2, axis=1, keepdims=True)))
+    print("iB m=1: %.3g of the bound" % float(np.max(np.abs(g) / lim)))
+    assert np.all(np.abs(g) <= lim)
+
+
+def test_ib_fullsize_512_in_512_cubes(torch_cuda, ora):
+    # the measured workload: 512^3, 64 shells of width 2 k_f, 8^3 cubes of 64^3
+    _check(torch_cuda, ora, 512, 64, 2.0, 8, 4242)
