@@ -296,6 +296,8 @@ def main():
     torch.cuda.synchronize()
     ib_ms = s0.elapsed_time(s1) / 5
     del iws
+    sk_bytes = skew_alg_bytes(args.n, edges)
+    ib_bytes = ib_alg_bytes(args.n, edges, ib_m)
     # density input stage (CIC + interlacing + forward FFT) on the particle workload's
     # shape: 256^3 grid, 4 Mi particles (uniform positions: the cost does not depend on them)
     dn, dnp = 256, 4 * 2 ** 20
@@ -400,9 +402,14 @@ def main():
                               "particles_per_s": dnp / (den_ms / 1e3), "algorithmic_bytes": den_bytes,
                               "achieved_gbs": den_bytes / (den_ms / 1e3) / 1e9,
                               "frac_hbm": den_bytes / (den_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
-            "skew_spectrum": {"ms": sk_ms, "shells_per_s": args.shells * 3 / (sk_ms / 1e3)},
+            "skew_spectrum": {"ms": sk_ms, "shells_per_s": args.shells * 3 / (sk_ms / 1e3),
+                              "algorithmic_bytes": sk_bytes, "achieved_gbs": sk_bytes / (sk_ms / 1e3) / 1e9,
+                              "frac_hbm": sk_bytes / (sk_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
             "integrated_bispectrum": {"ms": ib_ms, "subcubes": ib_m ** 3, "subcube_side": args.n // ib_m,
-                                      "shells_per_s": args.shells * 3 / (ib_ms / 1e3)},
+                                      "shells_per_s": args.shells * 3 / (ib_ms / 1e3),
+                                      "algorithmic_bytes": ib_bytes,
+                                      "achieved_gbs": ib_bytes / (ib_ms / 1e3) / 1e9,
+                                      "frac_hbm": ib_bytes / (ib_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
             "power_multipoles": {"ms": pw_ms, "shells_per_s": args.shells * 3 / (pw_ms / 1e3),
                                  "algorithmic_bytes": pw_bytes, "achieved_gbs": pw_bytes / (pw_ms / 1e3) / 1e9,
                                  "frac_hbm": pw_bytes / (pw_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}}
@@ -458,6 +465,42 @@ def fft_alg_bytes(n, edges):
     nf = 3 * (len(edges) - 1)
     per = 8 * (nK * nK * nKz) + 2 * 8 * (nK * n * nKz) + 2 * 8 * (n * n * nKz) + 4 * n ** 3
     return float(nf * per)
+
+
+def raw_fft_bytes(n):
+    """HBM bytes of the unpruned inverse real FFT of delta (all modes but the
+    mean): the half spectrum read, the two complex64 intermediates written and
+    read once, the FP32 field written."""
+    h = 8 * n * n * (n // 2 + 1)
+    return float(5 * h + 4 * n ** 3)
+
+
+def power_read_bytes(n, edges, m=1):
+    """Complex64 modes the shell sums read: the box |f| <= K of each of the
+    m^3 spectra of side n/m (K from the top edge, in units of the box's k_f)."""
+    s = n // m
+    K = 0
+    while (K + 1) ** 2 * m * m < edges[-1] ** 2:
+        K += 1
+    nK, nKz = min(s, 2 * K + 1), min(s // 2 + 1, K + 1)
+    return float(8 * m ** 3 * nK * nK * nKz)
+
+
+def skew_alg_bytes(n, edges):
+    """Skew spectrum: inverse FFT, the forward FFT of the square (field read,
+    spectrum written, then read and written by each of two passes), the cross
+    sums reading delta and Q."""
+    h = 8 * n * n * (n // 2 + 1)
+    return raw_fft_bytes(n) + 4 * n ** 3 + 5 * h + 2 * power_read_bytes(n, edges)
+
+
+def ib_alg_bytes(n, edges, m):
+    """Integrated bispectrum: inverse FFT, the sub-cube forward FFTs (field
+    read, m^3 spectra written, then read and written by each of two passes),
+    the weighted sums reading the sub-cube spectra."""
+    s = n // m
+    hs = 8 * m ** 3 * s * s * (s // 2 + 1)
+    return raw_fft_bytes(n) + 4 * n ** 3 + 5 * hs + power_read_bytes(n, edges, m)
 
 
 if __name__ == "__main__":
