@@ -418,7 +418,62 @@ class Modal:
             pass
 
 
-class Bispectrum:
+class Spectra:
+    """A plan's shell tables without the bispectrum workspace or counts: the
+    skew spectrum and the integrated bispectrum, each with a workspace of its
+    own, on the plan's shells and multipoles."""
+
+    def __init__(self, n, box, edges, ells=(0, 2, 4)):
+        self.n, self.box, self.ells = int(n), float(box), tuple(ells)
+        self.edges = [float(e) for e in edges]
+        self.plan = bsp_plan_create(n, box, edges, ells, BSP_FP32, 0)
+
+    def skew(self, delta_k, ws=None, stream=None):
+        """Skew-spectrum multipoles S [n_ell][n_shells] and mode counts Nk (FP64,
+        device) on the plan's shells; ``ws`` an optional reusable uint8 CUDA
+        tensor of bsp_skew_workspace_size bytes."""
+        import torch
+
+        nb = ctypes.c_size_t()
+        _check(load().bsp_skew_workspace_size(self.plan, ctypes.byref(nb)), "bsp_skew_workspace_size")
+        if ws is None or ws.numel() < nb.value:
+            ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+        S = torch.empty((len(self.ells), len(self.edges) - 1), dtype=torch.float64, device="cuda")
+        Nk = torch.empty(len(self.edges) - 1, dtype=torch.float64, device="cuda")
+        _check(load().bsp_skew_compute(self.plan, _dptr(delta_k), _dptr(ws), int(ws.numel()), _stream_handle(stream),
+                                       _dptr(S), _dptr(Nk)), "bsp_skew_compute")
+        return S, Nk
+
+    def integrated(self, delta_k, m, ws=None, stream=None):
+        """Integrated-bispectrum multipoles iB [n_ell][n_shells] over m^3
+        sub-cubes and the per-cube mode counts Nk (FP64, device) on the plan's
+        shells; ``ws`` an optional reusable uint8 CUDA tensor of
+        bsp_ib_workspace_size bytes."""
+        import torch
+
+        nb = ctypes.c_size_t()
+        _check(load().bsp_ib_workspace_size(self.plan, int(m), ctypes.byref(nb)), "bsp_ib_workspace_size")
+        if ws is None or ws.numel() < nb.value:
+            ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+        iB = torch.empty((len(self.ells), len(self.edges) - 1), dtype=torch.float64, device="cuda")
+        Nk = torch.empty(len(self.edges) - 1, dtype=torch.float64, device="cuda")
+        _check(load().bsp_ib_compute(self.plan, _dptr(delta_k), int(m), _dptr(ws), int(ws.numel()),
+                                     _stream_handle(stream), _dptr(iB), _dptr(Nk)), "bsp_ib_compute")
+        return iB, Nk
+
+    def close(self):
+        if getattr(self, "plan", None):
+            bsp_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Bispectrum(Spectra):
     """A plan plus its device workspace (PyTorch-allocated), counts done on
     construction.  ``compute(delta_k)`` returns B [n_ell][n_bins] (FP64,
     device) for a complex64 [n][n][n/2+1] CUDA tensor."""
@@ -463,39 +518,6 @@ class Bispectrum:
         Nk = torch.empty(len(self.edges) - 1, dtype=torch.float64, device="cuda")
         bsp_power_compute(self.plan, delta_k, P, self.ws, nbar, stream, Nk)
         return P, Nk
-
-    def skew(self, delta_k, ws=None, stream=None):
-        """Skew-spectrum multipoles S [n_ell][n_shells] and mode counts Nk (FP64,
-        device) on the plan's shells; ``ws`` an optional reusable uint8 CUDA
-        tensor of bsp_skew_workspace_size bytes."""
-        import torch
-
-        nb = ctypes.c_size_t()
-        _check(load().bsp_skew_workspace_size(self.plan, ctypes.byref(nb)), "bsp_skew_workspace_size")
-        if ws is None or ws.numel() < nb.value:
-            ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
-        S = torch.empty((len(self.ells), len(self.edges) - 1), dtype=torch.float64, device="cuda")
-        Nk = torch.empty(len(self.edges) - 1, dtype=torch.float64, device="cuda")
-        _check(load().bsp_skew_compute(self.plan, _dptr(delta_k), _dptr(ws), int(ws.numel()), _stream_handle(stream),
-                                       _dptr(S), _dptr(Nk)), "bsp_skew_compute")
-        return S, Nk
-
-    def integrated(self, delta_k, m, ws=None, stream=None):
-        """Integrated-bispectrum multipoles iB [n_ell][n_shells] over m^3
-        sub-cubes and the per-cube mode counts Nk (FP64, device) on the plan's
-        shells; ``ws`` an optional reusable uint8 CUDA tensor of
-        bsp_ib_workspace_size bytes."""
-        import torch
-
-        nb = ctypes.c_size_t()
-        _check(load().bsp_ib_workspace_size(self.plan, int(m), ctypes.byref(nb)), "bsp_ib_workspace_size")
-        if ws is None or ws.numel() < nb.value:
-            ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
-        iB = torch.empty((len(self.ells), len(self.edges) - 1), dtype=torch.float64, device="cuda")
-        Nk = torch.empty(len(self.edges) - 1, dtype=torch.float64, device="cuda")
-        _check(load().bsp_ib_compute(self.plan, _dptr(delta_k), int(m), _dptr(ws), int(ws.numel()),
-                                     _stream_handle(stream), _dptr(iB), _dptr(Nk)), "bsp_ib_compute")
-        return iB, Nk
 
     def raw(self, stream=None):
         import torch

@@ -336,7 +336,9 @@ struct bsp_plan {
     int fb_cap = 1;                   // FFT batch width the workspace was sized for
     int16_t* d_shell_of = nullptr;
     FieldDesc* d_fd_raw = nullptr;    // one field: delta on every mode but the mean (skew spectrum)
+    int n2top = 0;                    // largest |n|^2 in a shell
     int ib_m = 0;                     // integrated bispectrum: cubes per side of the cached shell table
+    int ib_n2top = 0;                 // largest |n_s|^2 of the sub-cube grid in a shell
     int16_t* d_shell_sub = nullptr;   // shell of each |n_s|^2 of the sub-cube grid (|n| = m |n_s|)
     cx<float>* d_tw32 = nullptr;
     cx<double>* d_tw64 = nullptr;
@@ -568,6 +570,8 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
             double lo = p->edges[s], hi = p->edges[s + 1];
             if ((double)n2 >= lo * lo && (double)n2 < hi * hi) { shell_of[n2] = (int16_t)s; break; }
         }
+    for (int n2 = 0; n2 <= g.n2max; ++n2)
+        if (shell_of[n2] >= 0) p->n2top = n2;
     std::vector<cx<double>> tw64(n);
     std::vector<cx<float>> tw32(n);
     for (int t = 0; t < n; ++t) {
@@ -1269,8 +1273,7 @@ bsp_status bsp_power_compute(bsp_plan* p, const void* delta_k, double nbar, void
     if (power_partial_bytes(nblocks, p->nsh, pe.n) > p->ws_bytes) return BSP_ENOMEM;
     const double V = p->box * p->box * p->box;
     cudaError_t e = launch_power((const cx<float>*)delta_k, nullptr, 1.0, p->geom, p->d_shell_of, p->nsh, pe, V, nbar,
-                                 nblocks,
-                                 (double*)ws, P, Nk, (cudaStream_t)stream);
+                                 nblocks, (double*)ws, P, Nk, (cudaStream_t)stream, 1, 0, 0, p->n2top);
     if (e != cudaSuccess) return cuda_fail(e, "power multipoles");
     return BSP_OK;
 }
@@ -1354,7 +1357,7 @@ bsp_status bsp_skew_compute(bsp_plan* p, const void* delta_k, void* ws, size_t w
     while (nblocks > 1 && power_partial_bytes(nblocks, p->nsh, pe.n) > room) nblocks /= 2;
     // Q = (V/n^3) x transform: the cross sum carries that factor
     e = launch_power((const cx<float>*)delta_k, t1, V / (double)n3, p->geom, p->d_shell_of, p->nsh, pe, V, 0.0,
-                     nblocks, (double*)t2, S, Nk, st);
+                     nblocks, (double*)t2, S, Nk, st, 1, 0, 0, p->n2top);
     if (e != cudaSuccess) return cuda_fail(e, "skew (shell sums)");
     return BSP_OK;
 }
@@ -1428,12 +1431,16 @@ bsp_status bsp_ib_compute(bsp_plan* p, const void* delta_k, int m, void* ws, siz
                     break;
                 }
         }
+        int top = 0;
+        for (int q = 0; q <= gs.n2max; ++q)
+            if (tab[q] >= 0) top = q;
         cudaFree(p->d_shell_sub);
         p->d_shell_sub = nullptr;
         p->ib_m = 0;
         bsp_status st = upload(&p->d_shell_sub, tab);
         if (st != BSP_OK) return st;
         p->ib_m = m;
+        p->ib_n2top = top;
     }
     const cudaStream_t st = (cudaStream_t)stream;
     char* base = (char*)ws;
@@ -1456,7 +1463,7 @@ bsp_status bsp_ib_compute(bsp_plan* p, const void* delta_k, int m, void* ws, siz
     // iB^l_a = (1/m^3) sum_c T_c(0) (V_s^2 / (V_s N_a)) sum_{n in a} w_l |T_c|^2
     //        = V_s (sum_c T_c(0) sum w_l |T_c|^2) / (m^3 N_a)
     e = launch_power(T, nullptr, Vs, gs, p->d_shell_sub, p->nsh, pe, 1.0, 0.0, L.nbx, (double*)(base + L.part), iB,
-                     Nk, st, nc, (size_t)s * s * (s / 2 + 1), 1);
+                     Nk, st, nc, (size_t)s * s * (s / 2 + 1), 1, p->ib_n2top);
     if (e != cudaSuccess) return cuda_fail(e, "integrated bispectrum (shell sums)");
     return BSP_OK;
 }

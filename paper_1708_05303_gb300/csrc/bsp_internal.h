@@ -170,11 +170,12 @@ size_t power_partial_bytes(int nblocks, int nsh, int nell);
 // With nbatch > 1, delta holds nbatch spectra bstride elements apart, each
 // summed by nblocks CTAs (partial: nbatch * nblocks slots); with dc_weight
 // every product of spectrum b is multiplied by Re delta_b(0), and Nk is the
-// count per spectrum.
+// count per spectrum.  Rows with f_x^2 + f_y^2 > n2top (the largest |n|^2 of
+// any shell, or g.n2max) are skipped.
 cudaError_t launch_power(const cx<float>* delta, const cx<float>* Q, double num_scale, const FftGeom& g,
                          const int16_t* shell_of, int nsh, const PowerEll& ells, double V, double nbar, int nblocks,
                          double* partial, double* P, double* Nk, cudaStream_t st, int nbatch = 1,
-                         size_t bstride = 0, int dc_weight = 0);
+                         size_t bstride = 0, int dc_weight = 0, int n2top = 1 << 30);
 
 // ---- launchers (bsp_modal.cu) ----
 cudaError_t launch_modal_assemble(const double* T, const double* U, const int* ells, int n_ell, int nf,

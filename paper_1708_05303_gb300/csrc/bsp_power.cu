@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
                                                                  const cx<float>* __restrict__ Q, FftGeom g,
                                                                  const int16_t* __restrict__ shell_of, int nsh,
                                                                  PowerEll ells, double* __restrict__ partial,
-                                                                 size_t bstride, int dc_weight) {
+                                                                 size_t bstride, int dc_weight, int n2top) {
     // per warp [2 nell + 1][nsh] FP64: sum w|d|^2 per l, sum w per l, mode count
     extern __shared__ double acc[];
     const int nell = ells.n, per = (2 * nell + 1) * nsh;
@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
         const int cx_ = (int)(r / g.nK), cy = (int)(r % g.nK);
         const int fx = g.pruned ? cx_ - g.K : (cx_ < N / 2 ? cx_ : cx_ - N);
         const int fy = g.pruned ? cy - g.K : (cy < N / 2 ? cy : cy - N);
+        if (fx * fx + fy * fy > n2top) continue;   // no mode of this row lies in a shell
         const int ix = (fx + N) % N, iy = (fy + N) % N;
         const cx<float>* row = delta + ((size_t)ix * N + iy) * H;
         const size_t mo = ((size_t)((N - ix) % N) * N + (N - iy) % N) * H, ro = ((size_t)ix * N + iy) * H;
@@ -132,19 +133,37 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
     }
 }
 
-__global__ void k_power_final(const double* __restrict__ partial, int nblocks, int nsh, int nell, double V,
-                              double nbar, double num_scale, int nbatch, double* __restrict__ P,
-                              double* __restrict__ Nk) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nell * nsh) return;
+constexpr int PF_THREADS = 128;
+
+// One CTA per output (l, shell): thread i sums the CTA slots i, i + 128, ...
+// in order, then a fixed tree over the threads (the same order on every run).
+__global__ void __launch_bounds__(PF_THREADS) k_power_final(const double* __restrict__ partial, int nblocks, int nsh,
+                                                            int nell, double V, double nbar, double num_scale,
+                                                            int nbatch, double* __restrict__ P,
+                                                            double* __restrict__ Nk) {
+    __shared__ double red[3][PF_THREADS];
+    const int t = blockIdx.x;
     const int l = t / nsh, s = t % nsh, per = (2 * nell + 1) * nsh;
     double sp = 0.0, sw = 0.0, sn = 0.0;
-    for (int b = 0; b < nblocks; ++b) {   // fixed order: deterministic
+    for (int b = threadIdx.x; b < nblocks; b += PF_THREADS) {
         const double* q = partial + (size_t)b * per;
         sp += q[l * nsh + s];
         sw += q[(nell + l) * nsh + s];
         sn += q[2 * nell * nsh + s];
     }
+    red[0][threadIdx.x] = sp;
+    red[1][threadIdx.x] = sw;
+    red[2][threadIdx.x] = sn;
+    __syncthreads();
+    for (int h = PF_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    sp = red[0][0];
+    sw = red[1][0];
+    sn = red[2][0];
     double v = 0.0;
     if (sn > 0.0) {
         v = num_scale * sp / (V * sn);
@@ -163,7 +182,7 @@ size_t power_partial_bytes(int nblocks, int nsh, int nell) {
 cudaError_t launch_power(const cx<float>* delta, const cx<float>* Q, double num_scale, const FftGeom& g,
                          const int16_t* shell_of, int nsh, const PowerEll& ells, double V, double nbar, int nblocks,
                          double* partial, double* P, double* Nk, cudaStream_t st, int nbatch, size_t bstride,
-                         int dc_weight) {
+                         int dc_weight, int n2top) {
     const size_t smem = (size_t)PW_WARPS * (2 * ells.n + 1) * nsh * sizeof(double);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     static size_t set = 0;   // raised once per size, never inside a graph capture
@@ -176,10 +195,9 @@ cudaError_t launch_power(const cx<float>* delta, const cx<float>* Q, double num_
     }
     if (nbatch < 1 || nbatch > 65535 || (nbatch > 1 && Q)) return cudaErrorInvalidValue;
     k_power_partial<<<dim3(nblocks, nbatch), 32 * PW_WARPS, smem, st>>>(delta, Q, g, shell_of, nsh, ells, partial,
-                                                                        bstride, dc_weight);
-    const int nt = ells.n * nsh;
-    k_power_final<<<(nt + 127) / 128, 128, 0, st>>>(partial, nblocks * nbatch, nsh, ells.n, V, nbar, num_scale,
-                                                    nbatch, P, Nk);
+                                                                        bstride, dc_weight, n2top);
+    k_power_final<<<ells.n * nsh, PF_THREADS, 0, st>>>(partial, nblocks * nbatch, nsh, ells.n, V, nbar, num_scale,
+                                                        nbatch, P, Nk);
     return cudaGetLastError();
 }
 

@@ -92,3 +92,21 @@ def _ib_single_cube_bound(ora, dk, n, edges, g, nk):
 def test_ib_fullsize_512_in_512_cubes(torch_cuda, ora):
     # the measured workload: 512^3, 64 shells of width 2 k_f, 8^3 cubes of 64^3
     _check(torch_cuda, ora, 512, 64, 2.0, 8, 4242)
+
+
+def test_ib_spectra_handle_matches_bispectrum(torch_cuda):
+    # the plan-only handle (no bispectrum workspace, no counts) runs the same path
+    from paper_1708_05303_gb300 import bsp
+
+    n, edges = 64, linear_edges(16, 2.0)
+    dk, _ = make_field(FieldModel(n=n, box=BOX, sigma_g=0.3), 7)
+    d = torch_cuda.from_numpy(dk).cuda()
+    a = bsp.Spectra(n, BOX, edges)
+    b = bsp.Bispectrum(n, BOX, edges, (0, 2, 4))
+    ia, _ = a.integrated(d, 4)
+    ib, _ = b.integrated(d, 4)
+    sa, _ = a.skew(d)
+    sb, _ = b.skew(d)
+    assert torch_cuda.equal(ia, ib) and torch_cuda.equal(sa, sb)
+    a.close()
+    b.close()
