@@ -33,6 +33,9 @@ __device__ __forceinline__ float legendre_w(int ell, int fz2, int n2) {
 
 constexpr int PW_WARPS = 8;   // warps per CTA
 
+// SHOT: also sum w_l per shell (the weights of the shot-noise term); without
+// it those sums stay 0 and the scan carries 4 values instead of 7.
+template <bool SHOT>
 __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>* __restrict__ delta,
                                                                  const cx<float>* __restrict__ Q, FftGeom g,
                                                                  const int16_t* __restrict__ shell_of, int nsh,
@@ -97,18 +100,20 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
                     for (int l = 0; l < nell; ++l) {
                         const float w = legendre_w(ells.ell[l], fz * fz, n2);
                         v[l] = w * p;
-                        v[3 + l] = w * h;
+                        if (SHOT) v[4 + l] = w * h;
                     }
-                    v[6] = h;
+                    v[3] = h;
                 }
             }
             if (__all_sync(0xffffffffu, s < 0)) continue;
+            // v: [0, 3) w_l p, [3] the mode count, [4, 7) w_l (SHOT only)
+            constexpr int NV = SHOT ? 7 : 4;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int so = __shfl_up_sync(0xffffffffu, s, o);
                 const bool take = lane >= o && so == s;
 #pragma unroll
-                for (int t = 0; t < 7; ++t) {
+                for (int t = 0; t < NV; ++t) {
                     const float x = __shfl_up_sync(0xffffffffu, v[t], o);
                     if (take) v[t] += x;
                 }
@@ -117,9 +122,9 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_power_partial(const cx<float>
             if (s >= 0 && (lane == 31 || snext != s)) {
                 for (int l = 0; l < nell; ++l) {
                     mine[l * nsh + s] += (double)v[l];
-                    mine[(nell + l) * nsh + s] += (double)v[3 + l];
+                    if (SHOT) mine[(nell + l) * nsh + s] += (double)v[4 + l];
                 }
-                mine[2 * nell * nsh + s] += (double)v[6];
+                mine[2 * nell * nsh + s] += (double)v[3];
             }
             __syncwarp();
         }
@@ -185,17 +190,18 @@ cudaError_t launch_power(const cx<float>* delta, const cx<float>* Q, double num_
                          int dc_weight, int n2top) {
     const size_t smem = (size_t)PW_WARPS * (2 * ells.n + 1) * nsh * sizeof(double);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    static size_t set = 0;   // raised once per size, never inside a graph capture
+    const bool shot = nbar > 0.0;
+    auto kern = shot ? k_power_partial<true> : k_power_partial<false>;
+    static size_t set[2] = {0, 0};   // raised once per size and variant, never inside a graph capture
     cudaError_t e;
-    if (smem > 48 * 1024 && smem > set) {
-        if ((e = cudaFuncSetAttribute(k_power_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
+    if (smem > 48 * 1024 && smem > set[shot]) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
-        set = smem;
+        set[shot] = smem;
     }
     if (nbatch < 1 || nbatch > 65535 || (nbatch > 1 && Q)) return cudaErrorInvalidValue;
-    k_power_partial<<<dim3(nblocks, nbatch), 32 * PW_WARPS, smem, st>>>(delta, Q, g, shell_of, nsh, ells, partial,
-                                                                        bstride, dc_weight, n2top);
+    kern<<<dim3(nblocks, nbatch), 32 * PW_WARPS, smem, st>>>(delta, Q, g, shell_of, nsh, ells, partial, bstride,
+                                                             dc_weight, n2top);
     k_power_final<<<ells.n * nsh, PF_THREADS, 0, st>>>(partial, nblocks * nbatch, nsh, ells.n, V, nbar, num_scale,
                                                         nbatch, P, Nk);
     return cudaGetLastError();
