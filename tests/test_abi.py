@@ -75,3 +75,25 @@ def test_null_arguments(lib):
     n = ctypes.c_int()
     assert lib.bsp_plan_bins(None, ctypes.byref(n), None, None) == bsp.BSP_EINVAL
     lib.bsp_plan_destroy(None)
+
+
+def test_null_arguments_of_the_spectra_entry_points(lib):
+    # power, density, skew and integrated-bispectrum calls reject missing
+    # handles and bad sizes on the host, before any CUDA call
+    import ctypes
+
+    from paper_1708_05303_gb300 import bsp
+
+    nb = ctypes.c_size_t()
+    assert lib.bsp_power_compute(None, None, 0.0, None, None, None, None) == bsp.BSP_EINVAL
+    assert lib.bsp_skew_workspace_size(None, ctypes.byref(nb)) == bsp.BSP_EINVAL
+    assert lib.bsp_skew_compute(None, None, None, 0, None, None, None) == bsp.BSP_EINVAL
+    assert lib.bsp_ib_workspace_size(None, 8, ctypes.byref(nb)) == bsp.BSP_EINVAL
+    assert lib.bsp_ib_compute(None, None, 8, None, 0, None, None, None) == bsp.BSP_EINVAL
+    for n in (63, 14, 6):   # odd, a radix of 7, too small
+        assert lib.bsp_density_workspace_size(n, ctypes.byref(nb)) == bsp.BSP_EINVAL
+    assert lib.bsp_density_workspace_size(64, None) == bsp.BSP_EINVAL
+    assert lib.bsp_density_workspace_size(64, ctypes.byref(nb)) == bsp.BSP_OK
+    # two FP32 grids and two half spectra at least
+    assert nb.value >= 2 * 64 ** 3 * 4 + 2 * 64 * 64 * 33 * 8
+    assert lib.bsp_density_cic(64, 1000.0, 0, None, None, 0, None, None, None) == bsp.BSP_EINVAL
