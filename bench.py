@@ -439,6 +439,10 @@ def main():
                                 "speedup_step": ms32 / ms, "speedup_contraction": ph32[1] / con_ms,
                                 "max_rel_dev_vs_fp32": dev, "steps": k32}
         ref.close()
+    # cuFFT as a timed comparison only (never on the path): a full, unpruned
+    # C2R transform of one n^3 field beside this library's per-field filter +
+    # pruned inverse FFT + 16-bit split
+    line["cufft_compare"] = cufft_compare(d, args.n, fft_ms / (3 * args.shells), stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         info = cpu_sample(dk, args.n, edges)
         step_s = info["t_full"] + 3 * args.shells * info["t_field"] + outputs * info["t_bin"]
@@ -450,6 +454,37 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def cufft_compare(delta_k, n, ours_ms_per_field, stream=None, reps=10):
+    """Time torch.fft.irfftn (cuFFT) on the n^3 half spectrum: the full
+    complex-to-real transform of one field, no filter and no pruning.  Any
+    failure is reported in the result instead of raised."""
+    import torch
+
+    try:
+        dev = delta_k.device
+        out = None
+        for _ in range(3):
+            out = torch.fft.irfftn(delta_k, s=(n, n, n), dim=(0, 1, 2))
+        if dev.type != "cuda":
+            return {"error": "no CUDA device"}
+        st = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(reps):
+                out = torch.fft.irfftn(delta_k, s=(n, n, n), dim=(0, 1, 2))
+            b.record(st)
+            torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        del out
+        return {"cufft_ms_per_field": ms, "ours_ms_per_field": ours_ms_per_field,
+                "what": "cuFFT (torch.fft.irfftn): full unpruned C2R of one %d^3 field, FP32; ours: shell/Legendre "
+                        "filter + pruned C2R + hi/lo split of one field (filter_fft phase / fields per step)" % n}
+    except Exception as e:   # a comparison only: never fail the run for it
+        return {"error": "%s: %s" % (type(e).__name__, str(e)[:200])}
 
 
 def fft_alg_bytes(n, edges):
