@@ -204,6 +204,7 @@ def main():
 
     B.build()
     from paper_1708_05303_gb300 import bsp
+    from paper_1708_05303_gb300.dist import max_over_ranks
 
     edges, desc = workload(args.n, args.shells, args.width)
     dk = make_input(args.n)
@@ -242,10 +243,7 @@ def main():
     phase, ncalls, launches = bsp.bsp_phase_times(est.plan)
     bsp.bsp_set_profiling(est.plan, False)
     phase = [p / max(ncalls, 1) for p in phase]
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device="cuda")   # the slowest rank's time
     value = outputs * world / (ms / 1e3)
 
     # power-spectrum multipoles on the same shells (Eq. PowSpecMultipole): one pass over the
@@ -336,10 +334,7 @@ def main():
             est.compute_host(host.numpy(), Bh.numpy())
         dt = (time.perf_counter() - t0) / args.steps
         barrier()
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, device="cuda")
         e2e = {"value": outputs * world / dt, "unit": "bins/s", "h2d_bytes_per_step": int(host.numel() * 8),
                "d2h_bytes_per_step": int(Bh.numel() * 8)}
 
