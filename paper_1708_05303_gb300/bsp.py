@@ -230,6 +230,17 @@ def bsp_plan_bins(plan: int):
     return abc, cnt
 
 
+def aliased_bins(n: int, edges, bins) -> np.ndarray:
+    """Per bin (a, b, c): True where the grid's mod-n triangle sum may hold
+    wrapped triangles, q1 + q2 + q3 a nonzero multiple of n.  Each component
+    of a mode of shell i is below hi_i in size, so that needs
+    hi_a + hi_b + hi_c > n; unflagged bins hold exactly the triangles of the
+    continuum closure q1 + q2 + q3 = 0.  Host metadata from the edges."""
+    e = np.asarray(edges, dtype=np.float64)
+    b = np.asarray(bins, dtype=np.int64).reshape(-1, 3)
+    return (e[b[:, 0] + 1] + e[b[:, 1] + 1] + e[b[:, 2] + 1]) > n
+
+
 def bsp_compute(plan: int, delta_k, B, ws, nbar: float = 0.0, stream=None):
     _check(load().bsp_compute(plan, _dptr(delta_k), float(nbar), _dptr(ws), _stream_handle(stream), _dptr(B)),
            "bsp_compute")
