@@ -222,6 +222,23 @@ bsp_status bsp_plan_share_counts(bsp_plan* dst, const bsp_plan* src);
 bsp_status bsp_plan_bins(const bsp_plan* plan, int* n_bins, int32_t* abc, double* counts);
 
 /*
+ * Aliasing flag per bin (host only, no GPU).  The FFT contraction computes
+ * the periodic sum over q1 + q2 + q3 = 0 (mod n); the paper's closure is
+ * q1 + q2 + q3 = 0 (Sec. 3.1, Eq. Bisp_ell_restrict).  The two differ only
+ * for bins that can hold wrapped triangles, a nonzero multiple of n; every
+ * component of a mode of shell s is below hi_s = edges_kf[s+1] in size, so
+ * that needs hi_a + hi_b + hi_c > n.  flags[i] = 1 for such bins (they may
+ * hold wrapped triangles), 0 for bins whose sum is exactly the continuum
+ * closure's.
+ *   n, n_shells, edges_kf  the plan's grid and shells (as bsp_plan_create).
+ *   abc      host int32 [n_bins][3] shell indices in [0, n_shells).
+ *   flags    host int32 [n_bins] (out).
+ * BSP_EINVAL for bad edges or indices.
+ */
+bsp_status bsp_bins_aliased(int n, int n_shells, const double* edges_kf, int n_bins, const int32_t* abc,
+                            int32_t* flags);
+
+/*
  * B^l for every valid bin (Eq. Standard_ell_Estim): enqueue filter ->
  * inverse FFTs -> contraction -> FP64 reduction and normalisation.
  *   delta_k  device, complex64 [n][n][n/2+1] (read only).
@@ -388,27 +405,37 @@ bsp_status bsp_phase_times(bsp_plan* plan, double* ms, int* ncalls, int* launche
 
 /*
  * Triple sums without any device allocation.  The paper has no counterpart:
- * this serves callers that cannot call cudaMalloc (a CUDA graph under
- * capture, a host runtime that owns all device memory in a fixed pool, a
- * hard memory budget).
+ * this serves callers that cannot call cudaMalloc -- a host runtime that
+ * hands out all device memory from its own fixed pool (an allocation behind
+ * its back breaks its accounting, or fails once the pool holds the whole
+ * device), or an embedded caller with a hard memory budget that must know,
+ * when the library loads, every byte the library will hold.
  *
  *   T[t] = sum_{x < npts} F_i(x) F_j(x) F_k(x),  (i, j, k) = triplets[3t..3t+2],
  *
  * over caller fields F_f = fields + f * npts (device, FP32, [nfields][npts],
  * 16-byte aligned).  triplets is HOST int32 [ntrip][3] with every index in
- * [0, nfields); T is device FP64 [ntrip] (8-byte aligned), written.  Sums
- * use FP32 products folded 64 at a time into compensated FP32 pairs, then
- * FP64 across segments (the same accuracy as the BSP_FP32 contraction).
+ * [0, nfields) (checked on the host before anything is enqueued); T is
+ * device FP64 [ntrip] (8-byte aligned), written.  Sums use FP32 products
+ * folded 64 at a time into compensated FP32 pairs, then FP64 across segments
+ * (the same accuracy as the BSP_FP32 contraction).
  *
  * Scratch: a 131 072-triplet list (1.5 MiB) and 2 097 152 FP64 partial sums
  * (16 MiB) live in fixed device arrays that every GPU loading the library
  * holds until the process exits.  ntrip above 131 072 is rejected with
- * BSP_EINVAL.  Every call reuses the same arrays; nothing in them needs to
- * start at zero (each partial is written before it is read), but calls that
- * overlap on the GPU (different streams, or host threads) race on them.
- * The first call on each device looks up the arrays' device addresses;
- * make that first call before any stream capture.  Asynchronous on
- * `stream` except for the triplet upload from pageable host memory.
+ * BSP_EINVAL.  Every call reuses the same arrays and they keep the last
+ * call's contents; nothing in them needs to start at zero (each partial is
+ * written before it is read), but calls that overlap on the GPU (different
+ * streams, or host threads) race on them.  The first call on each device
+ * looks up the arrays' device addresses (cudaGetSymbolAddress, synchronous);
+ * make that first call before any stream capture begins.
+ *
+ * The triplet list is copied with cudaMemcpyAsync on `stream`.  From
+ * pageable host memory the call returns once the copy has been staged; from
+ * pinned (page-locked) host memory the copy runs when the stream reaches it,
+ * so a pinned `triplets` buffer must stay allocated and unchanged until
+ * then.  The kernels run asynchronously on `stream`.  CUDA failures return
+ * BSP_ECUDA with the CUDA error text in bsp_last_error().
  */
 bsp_status bsp_triple_sums_static(const float* fields, size_t npts, int nfields,
                                   const int32_t* triplets, int ntrip, double* T, void* stream);

@@ -44,6 +44,7 @@ _SIGS = [
     ("bsp_host_staging_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("bsp_counts", ctypes.c_int, [_P, _P, _P]),
     ("bsp_plan_bins", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P, _P]),
+    ("bsp_bins_aliased", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     ("bsp_plan_share_counts", ctypes.c_int, [_P, _P]),
     ("bsp_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
     ("bsp_compute_host", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
@@ -230,15 +231,16 @@ def bsp_plan_bins(plan: int):
     return abc, cnt
 
 
-def aliased_bins(n: int, edges, bins) -> np.ndarray:
+def bsp_bins_aliased(n: int, edges, bins) -> np.ndarray:
     """Per bin (a, b, c): True where the grid's mod-n triangle sum may hold
-    wrapped triangles, q1 + q2 + q3 a nonzero multiple of n.  Each component
-    of a mode of shell i is below hi_i in size, so that needs
-    hi_a + hi_b + hi_c > n; unflagged bins hold exactly the triangles of the
-    continuum closure q1 + q2 + q3 = 0.  Host metadata from the edges."""
-    e = np.asarray(edges, dtype=np.float64)
-    b = np.asarray(bins, dtype=np.int64).reshape(-1, 3)
-    return (e[b[:, 0] + 1] + e[b[:, 1] + 1] + e[b[:, 2] + 1]) > n
+    wrapped triangles (the library's flag, hi_a + hi_b + hi_c > n); host
+    only."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    b = np.ascontiguousarray(bins, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros(b.shape[0], dtype=np.int32)
+    _check(load().bsp_bins_aliased(int(n), len(e) - 1, e.ctypes.data, int(b.shape[0]), b.ctypes.data,
+                                   out.ctypes.data), "bsp_bins_aliased")
+    return out.astype(bool)
 
 
 def bsp_compute(plan: int, delta_k, B, ws, nbar: float = 0.0, stream=None):
@@ -509,6 +511,8 @@ class Bispectrum(Spectra):
         else:
             bsp_counts(self.plan, self.ws, stream)
         self.bins, self.counts = bsp_plan_bins(self.plan)
+        # bins whose mod-n sum may hold wrapped triangles (the library's flag)
+        self.aliased = bsp_bins_aliased(self.n, self.edges, self.bins)
         self.B = torch.empty((len(self.ells), len(self.bins)), dtype=torch.float64, device="cuda")
 
     def compute(self, delta_k, nbar: float = 0.0, stream=None):

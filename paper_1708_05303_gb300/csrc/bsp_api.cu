@@ -28,6 +28,12 @@ bsp_status cuda_fail(cudaError_t e, const char* where) {
     g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
     return BSP_ECUDA;
 }
+}  // namespace
+
+bsp_status bsp::record_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+
+namespace {
+
 #define CK(call)                                              \
     do {                                                      \
         cudaError_t e_ = (call);                              \
@@ -926,6 +932,22 @@ bsp_status bsp_plan_bins(const bsp_plan* p, int* n_bins, int32_t* abc, double* c
             for (int k = 0; k < 3; ++k) abc[3 * i + k] = p->bins[i][k];
         if (counts) counts[i] = p->counts[i];
     }
+    return BSP_OK;
+}
+
+bsp_status bsp_bins_aliased(int n, int n_shells, const double* edges_kf, int n_bins, const int32_t* abc,
+                            int32_t* flags) {
+    if (n < 2 || n_shells < 1 || !edges_kf || n_bins < 0 || (n_bins && (!abc || !flags))) return BSP_EINVAL;
+    for (int i = 0; i <= n_shells; ++i)
+        if (!(edges_kf[i] > 0) || !std::isfinite(edges_kf[i]) || (i && !(edges_kf[i] > edges_kf[i - 1])))
+            return BSP_EINVAL;
+    for (int i = 0; i < 3 * n_bins; ++i)
+        if (abc[i] < 0 || abc[i] >= n_shells) return BSP_EINVAL;
+    // a mode of shell s has every component below hi_s in size, so q1 + q2 + q3
+    // can only be a nonzero multiple of n when hi_a + hi_b + hi_c > n
+    for (int i = 0; i < n_bins; ++i)
+        flags[i] = edges_kf[abc[3 * i] + 1] + edges_kf[abc[3 * i + 1] + 1] + edges_kf[abc[3 * i + 2] + 1] > (double)n
+                       ? 1 : 0;
     return BSP_OK;
 }
 

@@ -6,7 +6,13 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/bsp.h"
+
 namespace bsp {
+
+// Record `where: <CUDA error text>` as this thread's bsp_last_error() and
+// return BSP_ECUDA (defined in bsp_api.cu).
+bsp_status record_cuda_error(cudaError_t e, const char* where);
 
 template <typename R>
 struct __align__(2 * sizeof(R)) cx {

@@ -1,13 +1,15 @@
 // bsp_noalloc.cu -- triple sums over caller-provided fields without any
 // device allocation.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA graph
-// being captured, a host runtime whose device memory is owned by another
-// allocator with a fixed pool, or an embedded caller with a hard memory
-// budget.  bsp_triple_sums_static serves them: the caller passes the fields
-// and the output, and the two scratch areas the reduction needs -- the
-// triplet list and the per-segment partial sums -- live in file-scope device
-// arrays of fixed size, reserved on every device that loads the library.
+// Some callers cannot call cudaMalloc: a host runtime that hands out all
+// device memory from its own fixed pool (an allocation behind its back would
+// break its accounting or fail once the pool holds the whole device), or an
+// embedded caller with a hard memory budget that must know, when the library
+// loads, every byte the library will ever hold.  bsp_triple_sums_static
+// serves them: the caller passes the fields and the output, and the two
+// scratch areas the reduction needs -- the triplet list and the per-segment
+// partial sums -- live in file-scope device arrays of fixed size, reserved on
+// every device that loads the library.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,9 +93,11 @@ bsp_status na_setup(int dev, NaDevice** out) {
     NaDevice& d = g_na_dev[dev];
     if (!d.ready) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_na_triplets) != cudaSuccess) return BSP_ECUDA;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_na_triplets);
+        if (e != cudaSuccess) return bsp::record_cuda_error(e, "bsp_triple_sums_static: cudaGetSymbolAddress(triplets)");
         d.triplets = (int*)p;
-        if (cudaGetSymbolAddress(&p, g_na_partials) != cudaSuccess) return BSP_ECUDA;
+        e = cudaGetSymbolAddress(&p, g_na_partials);
+        if (e != cudaSuccess) return bsp::record_cuda_error(e, "bsp_triple_sums_static: cudaGetSymbolAddress(partials)");
         d.partials = (double*)p;
         d.ready = true;
     }
@@ -112,14 +116,15 @@ extern "C" bsp_status bsp_triple_sums_static(const float* fields, size_t npts, i
     for (int i = 0; i < 3 * ntrip; ++i)
         if (triplets[i] < 0 || triplets[i] >= nfields) return BSP_EINVAL;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return BSP_ECUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return bsp::record_cuda_error(e, "bsp_triple_sums_static: cudaGetDevice");
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return BSP_EUNSUPPORTED;
     NaDevice* d = nullptr;
     bsp_status s = na_setup(dev, &d);
     if (s != BSP_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(d->triplets, triplets, sizeof(int) * 3 * (size_t)ntrip, cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
-        return BSP_ECUDA;
+    e = cudaMemcpyAsync(d->triplets, triplets, sizeof(int) * 3 * (size_t)ntrip, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return bsp::record_cuda_error(e, "bsp_triple_sums_static: triplet upload");
     // segments: enough blocks to fill the GPU, each at least 4096 points,
     // and no more partial sums than the static array holds
     long long nseg = (long long)((npts + 4095) / 4096);
@@ -127,9 +132,20 @@ extern "C" bsp_status bsp_triple_sums_static(const float* fields, size_t npts, i
     nseg = std::min<long long>(nseg, NA_MAX_PARTIALS / ntrip);
     if (nseg < 1) nseg = 1;
     const size_t seg_len = (npts + nseg - 1) / nseg;
-    dim3 grid(ntrip, (unsigned)nseg);
-    k_na_partial<<<grid, NA_THREADS, 0, st>>>(fields, npts, d->triplets, seg_len, d->partials);
-    k_na_reduce<<<(ntrip + 255) / 256, 256, 0, st>>>(d->partials, ntrip, (int)nseg, T);
-    if (cudaGetLastError() != cudaSuccess) return BSP_ECUDA;
+    // each launch reports its own error (cudaLaunchKernelEx returns it; no
+    // cudaGetLastError that could pick up or clear an unrelated one)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ntrip, (unsigned)nseg);
+    cfg.blockDim = dim3(NA_THREADS);
+    cfg.stream = st;
+    const int* trip_dev = d->triplets;
+    double* part = d->partials;
+    e = cudaLaunchKernelEx(&cfg, k_na_partial, fields, npts, trip_dev, seg_len, part);
+    if (e != cudaSuccess) return bsp::record_cuda_error(e, "bsp_triple_sums_static: k_na_partial launch");
+    cfg.gridDim = dim3((unsigned)((ntrip + 255) / 256));
+    cfg.blockDim = dim3(256);
+    const double* cpart = part;
+    e = cudaLaunchKernelEx(&cfg, k_na_reduce, cpart, ntrip, (int)nseg, T);
+    if (e != cudaSuccess) return bsp::record_cuda_error(e, "bsp_triple_sums_static: k_na_reduce launch");
     return BSP_OK;
 }

@@ -13,9 +13,9 @@ grids):
   4. Kaiser redshift-space factor along z (the last axis):
      delta_s(k) = (1 + f mu^2) delta(k), mu = k_z/|k|, factor 1 at k = 0
      (the linear limit of Sec. 1, Eq. Delta2Deltas).
-  Optionally (the 256^3 particle workload): a lognormal Poisson sample of
-  delta_s with a fixed expected particle count, deposited by cloud-in-cell
-  on two grids offset by half a cell, interlaced and deconvolved.
+  Optionally (the 256^3 particle workload): positions of a lognormal Poisson
+  sample of delta_s with a fixed expected particle count (the deposit onto a
+  grid is the estimator's input stage, not done here).
 
 delta(k) is continuum normalised, delta(k) = (V/n^3) sum_x delta_x e^{-ik.x},
 and returned as the complex64 half spectrum [n][n][n/2+1].
@@ -95,65 +95,11 @@ def make_field(model: FieldModel, seed: int, dtype=np.complex64):
     return dk.astype(dtype), amp
 
 
-def cic_interlaced(model: FieldModel, seed: int, n_particles: int = 4 * 2 ** 20,
-                   dtype=np.complex64):
-    """The particle workload: delta_s(x) from ``make_field`` -> lognormal rate
-    lambda_x proportional to exp(delta_s) with sum lambda = n_particles ->
-    Poisson counts per cell -> positions uniform within the cell -> CIC
-    deposit on grid 1 and on grid 2 (particles shifted by -H/2 per axis, H the
-    cell size, i.e. grid 2 sampled at +H/2) -> delta_i = count/nbar_cell - 1
-    -> delta(k) = [delta_1(k) + e^{-i k.(H/2)(1,1,1)} delta_2(k)]/2 divided by
-    prod_i sinc^2(pi n_i / n) (grid 2's cell j stands for position (j + 1/2) H,
-    hence the phase).  Returns (half spectrum, realised N_p, nbar)."""
-    n, box = model.n, model.box
-    dk, _ = make_field(model, seed, dtype=np.complex128)
-    ds = np.fft.irfftn(dk * (n ** 3 / box ** 3), s=(n, n, n), axes=(0, 1, 2))
-    lam = np.exp(ds - ds.max())
-    lam *= n_particles / lam.sum()
-    rng = np.random.Generator(np.random.PCG64(seed + 7919))
-    cnt = rng.poisson(lam).ravel()
-    npart = int(cnt.sum())
-    cell = np.repeat(np.arange(n ** 3), cnt)
-    cx, cy, cz = np.unravel_index(cell, (n, n, n))
-    pos = np.stack([cx, cy, cz], axis=1).astype(np.float64)
-    pos += rng.random((npart, 3))            # in cell units, [0, n)
-    grids = []
-    for shift in (0.0, -0.5):
-        p = (pos + shift) % n
-        i0 = np.floor(p).astype(np.int64)
-        t = p - i0
-        g = np.zeros(n ** 3)
-        for dx in (0, 1):
-            wx = t[:, 0] if dx else 1.0 - t[:, 0]
-            ix = (i0[:, 0] + dx) % n
-            for dy in (0, 1):
-                wy = t[:, 1] if dy else 1.0 - t[:, 1]
-                iy = (i0[:, 1] + dy) % n
-                for dz in (0, 1):
-                    wz = t[:, 2] if dz else 1.0 - t[:, 2]
-                    iz = (i0[:, 2] + dz) % n
-                    np.add.at(g, (ix * n + iy) * n + iz, wx * wy * wz)
-        nbar_cell = npart / n ** 3
-        grids.append(g.reshape(n, n, n) / nbar_cell - 1.0)
-    d1 = delta_k_from_real(grids[0], box)
-    d2 = delta_k_from_real(grids[1], box)
-    fx = _freqs(n)
-    fz = np.arange(n // 2 + 1, dtype=np.float64)
-    fz[n // 2] = -(n // 2)
-    phase = np.exp(-1j * math.pi / n * (fx[:, None, None] + fx[None, :, None] + fz[None, None, :]))
-    d = 0.5 * (d1 + phase * d2)
-    sx = np.sinc(fx / n)
-    sz = np.sinc(fz / n)
-    win = (sx[:, None, None] * sx[None, :, None] * sz[None, None, :]) ** 2
-    d /= win
-    nbar = npart / box ** 3
-    return d.astype(dtype), npart, nbar
-
-
 def poisson_positions(model: FieldModel, seed: int, n_particles: int = 4 * 2 ** 20) -> np.ndarray:
     """Particle positions (float32 [N_p][3], box units in [0, box)) of the
-    particle workload: lognormal rate from ``make_field`` as in
-    ``cic_interlaced``, Poisson counts per cell, uniform within the cell."""
+    particle workload: delta_s(x) from ``make_field`` -> lognormal rate
+    lambda_x proportional to exp(delta_s) with sum lambda = n_particles ->
+    Poisson counts per cell -> positions uniform within the cell."""
     n, box = model.n, model.box
     dk, _ = make_field(model, seed, dtype=np.complex128)
     ds = np.fft.irfftn(dk * (n ** 3 / box ** 3), s=(n, n, n), axes=(0, 1, 2))

@@ -97,3 +97,29 @@ def test_null_arguments_of_the_spectra_entry_points(lib):
     # two FP32 grids and two half spectra at least
     assert nb.value >= 2 * 64 ** 3 * 4 + 2 * 64 * 64 * 33 * 8
     assert lib.bsp_density_cic(64, 1000.0, 0, None, None, 0, None, None, None) == bsp.BSP_EINVAL
+
+
+def test_static_triple_sums_reject_on_host(lib):
+    # the allocation-free entry point checks sizes and indices before any CUDA
+    # call, so fake (never dereferenced) device addresses are enough here
+    import ctypes
+
+    import numpy as np
+
+    from paper_1708_05303_gb300 import bsp
+
+    fake_fields, fake_T = 1 << 20, 1 << 21
+    f = lib.bsp_triple_sums_static
+    ok = np.zeros((4, 3), dtype=np.int32)
+    assert f(fake_fields, 4096, 2, None, 4, fake_T, None) == bsp.BSP_EINVAL       # no triplets
+    assert f(None, 4096, 2, ok.ctypes.data, 4, fake_T, None) == bsp.BSP_EINVAL     # no fields
+    assert f(fake_fields + 4, 4096, 2, ok.ctypes.data, 4, fake_T, None) == bsp.BSP_EINVAL   # unaligned
+    assert f(fake_fields, 4096, 2, ok.ctypes.data, 0, fake_T, None) == bsp.BSP_EINVAL       # empty
+    bad = ok.copy()
+    bad[3, 2] = 2                                                                  # index == nfields
+    assert f(fake_fields, 4096, 2, bad.ctypes.data, 4, fake_T, None) == bsp.BSP_EINVAL
+    bad[3, 2] = -1
+    assert f(fake_fields, 4096, 2, bad.ctypes.data, 4, fake_T, None) == bsp.BSP_EINVAL
+    big = np.zeros((131073, 3), dtype=np.int32)                                    # above the fixed scratch
+    assert f(fake_fields, 4096, 2, big.ctypes.data, 131073, fake_T, None) == bsp.BSP_EINVAL
+    del ctypes

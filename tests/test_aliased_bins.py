@@ -1,11 +1,12 @@
-"""The aliased-bin flag against brute-force triangle counts on a 12^3 grid:
-bins it leaves unflagged hold the same triangles under the mod-n closure the
-FFT computes and under the exact closure q1 + q2 + q3 = 0."""
+"""The library's aliased-bin flag (bsp_bins_aliased, host only) against
+brute-force triangle counts on a 12^3 grid: bins it leaves unflagged hold the
+same triangles under the mod-n closure the FFT computes and under the exact
+closure q1 + q2 + q3 = 0."""
 import itertools
 
 import numpy as np
 
-from paper_1708_05303_gb300.bsp import aliased_bins
+import pytest
 
 
 def _modes(n, lo, hi):
@@ -17,12 +18,20 @@ def _wrap(v, n):
     return (v + n // 2) % n - n // 2
 
 
-def test_flag_matches_brute_force_closures():
+@pytest.fixture(scope="module")
+def flags_of():
+    from paper_1708_05303_gb300 import build, bsp
+
+    build.build()
+    return bsp.bsp_bins_aliased
+
+
+def test_flag_matches_brute_force_closures(flags_of):
     n, edges = 12, [1.0, 2.5, 4.0, 5.5, 7.0]
     ns = len(edges) - 1
     modes = [_modes(n, edges[i], edges[i + 1]) for i in range(ns)]
     bins = [(a, b, c) for a in range(ns) for b in range(a + 1) for c in range(b + 1)]
-    flag = aliased_bins(n, edges, bins)
+    flag = flags_of(n, edges, bins)
     differ = []
     for (a, b, c), fl in zip(bins, flag):
         q3 = -(modes[a][:, None, :] + modes[b][None, :, :]).reshape(-1, 3)
@@ -37,3 +46,12 @@ def test_flag_matches_brute_force_closures():
     # the grid does wrap some triangles, and only in flagged bins
     assert any(differ)
     assert all(f for f, d in zip(flag, differ) if d)
+
+
+def test_flag_rejects_bad_input(flags_of):
+    from paper_1708_05303_gb300 import bsp
+
+    with pytest.raises(bsp.BspError):
+        flags_of(12, [1.0, 2.5, 2.0], [(0, 0, 0)])       # edges not ascending
+    with pytest.raises(bsp.BspError):
+        flags_of(12, [1.0, 2.5, 4.0], [(2, 0, 0)])       # shell index out of range

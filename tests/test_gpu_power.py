@@ -6,7 +6,8 @@ geometries; shot noise; bit-identical repeats."""
 import numpy as np
 import pytest
 
-from paper_1708_05303_gb300.synth import FieldModel, cic_interlaced, linear_edges, make_field
+from paper_1708_05303_gb300.synth import FieldModel, linear_edges, make_field
+from particle_input import particle_delta
 
 pytestmark = pytest.mark.gpu
 BOX = 1000.0
@@ -55,7 +56,7 @@ def test_power_shot_noise_256(torch_cuda, ora):
     torch = torch_cuda
     n = 256
     edges = linear_edges(32)
-    dk, npart, nbar = cic_interlaced(FieldModel(n=n, box=BOX, sigma_g=0.3), 1708 + 1)
+    dk, npart, nbar = particle_delta(FieldModel(n=n, box=BOX, sigma_g=0.3), 1708 + 1)
     est = bsp.Bispectrum(n, BOX, edges, (0, 2, 4), shot_noise=True)
     P, Nk = est.power(torch.from_numpy(dk).cuda(), nbar=nbar)
     P = P.cpu().numpy()

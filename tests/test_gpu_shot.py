@@ -11,7 +11,8 @@ on sampled bins at 256^3 with 32 shells and 4 Mi expected particles.
 import numpy as np
 import pytest
 
-from paper_1708_05303_gb300.synth import FieldModel, cic_interlaced, linear_edges
+from paper_1708_05303_gb300.synth import FieldModel, linear_edges
+from particle_input import particle_delta
 
 pytestmark = pytest.mark.gpu
 BOX = 1000.0
@@ -34,7 +35,7 @@ def test_shot_noise_small_grid(torch_cuda, ora):
     torch = torch_cuda
     n = 32
     edges = linear_edges(8)
-    dk, npart, nbar = cic_interlaced(FieldModel(n=n, box=BOX, sigma_g=0.3), 77, n_particles=200_000)
+    dk, npart, nbar = particle_delta(FieldModel(n=n, box=BOX, sigma_g=0.3), 77, n_particles=200_000)
     est = bsp.Bispectrum(n, BOX, edges, (0, 2, 4), shot_noise=True)
     B = est.compute(torch.from_numpy(dk).cuda(), nbar=nbar).cpu().numpy()
     B0 = est.compute(torch.from_numpy(dk).cuda()).cpu().numpy()   # same plan, no subtraction
@@ -57,7 +58,7 @@ def test_shot_noise_256_sampled(torch_cuda, ora):
     torch = torch_cuda
     n = 256
     edges = linear_edges(32)
-    dk, npart, nbar = cic_interlaced(FieldModel(n=n, box=BOX, sigma_g=0.3), 1708 + 1)
+    dk, npart, nbar = particle_delta(FieldModel(n=n, box=BOX, sigma_g=0.3), 1708 + 1)
     est = bsp.Bispectrum(n, BOX, edges, (0, 2, 4), shot_noise=True)
     B = est.compute(torch.from_numpy(dk).cuda(), nbar=nbar).cpu().numpy()
     bins = [tuple(b) for b in est.bins]

@@ -1,12 +1,17 @@
-"""The allocation-free entry point bsp_triple_sums_static against the plan
-path, through the C ABI, on two calls in a row.
+"""The allocation-free entry point bsp_triple_sums_static, through the C ABI.
 
-Callers that cannot allocate device memory (a graph under capture, a fixed
-external pool) get triple sums from fixed library-owned scratch; its results
-must agree with the raw sums the normal bsp_compute path produces for the
-same fields, within the 1e-5 tolerance the parity tests use, and repeat
-exactly.  Collected last on purpose: it runs after every other test in a
-stop-at-first-failure run, and it also passes alone in a fresh process.
+Some callers cannot call cudaMalloc: a host runtime that hands out all device
+memory from its own fixed pool, or an embedded caller with a hard memory
+budget that must know up front every byte the library holds.  For them the
+library keeps its scratch (triplet list, per-segment partial sums) in fixed
+device arrays.  These tests check that entry point against the library's
+normal bsp_compute path and against the oracle's triple sums, within the
+1e-5 tolerance of the parity tests, on two calls in a row (the scratch keeps
+the previous call's contents), on a side stream, and in the case where the
+fixed partial-sum array caps the number of segments.
+
+Collected last on purpose: in a stop-at-first-failure run every other test
+has run before it; it also passes alone in a fresh process.
 """
 import numpy as np
 import pytest
@@ -16,7 +21,8 @@ from paper_1708_05303_gb300.synth import FieldModel, linear_edges, make_field
 pytestmark = pytest.mark.gpu
 
 
-def test_static_scratch_matches_plan_path_twice():
+@pytest.fixture(scope="module")
+def cuda():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -25,6 +31,16 @@ def test_static_scratch_matches_plan_path_twice():
     build.build()
     from paper_1708_05303_gb300 import bsp
 
+    return torch, bsp
+
+
+def gate(got, ref):
+    rms = np.sqrt(np.mean(ref ** 2))
+    return np.max(np.abs(got - ref) / np.maximum(np.abs(ref), rms))
+
+
+def test_static_scratch_matches_plan_path_and_oracle_twice(cuda, ora):
+    torch, bsp = cuda
     n, box = 32, 1000.0
     edges = linear_edges(8)
     ells = (0, 2, 4)
@@ -42,15 +58,48 @@ def test_static_scratch_matches_plan_path_twice():
         T = torch.full((len(trip),), float("nan"), dtype=torch.float64, device="cuda")
         bsp.bsp_triple_sums_static(fields, npts, nfields, trip, T)
         torch.cuda.synchronize()
-        outs.append(T.cpu().numpy().reshape(len(ells), -1))
-    ref = T_plan
-    rms = np.sqrt(np.mean(ref ** 2, axis=1, keepdims=True))
+        outs.append(T.cpu().numpy())
+    # the oracle's compensated FP64 triple sums of the very same FP32 fields
+    host = fields.cpu().numpy().reshape(nfields, npts).astype(np.float64)
+    T_ora, _ = ora.sum3(list(host), trip)
     for got in outs:
         assert np.all(np.isfinite(got))
-        assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), rms)) <= 1e-5
+        assert gate(got.reshape(len(ells), -1), T_plan) <= 1e-5
+        assert gate(got, T_ora) <= 1e-5
     assert np.array_equal(outs[0], outs[1])
     with pytest.raises(bsp.BspError):
         bad = trip.copy()
         bad[0, 0] = nfields
         bsp.bsp_triple_sums_static(fields, npts, nfields, bad, T)
     est.close()
+
+
+def test_static_scratch_capped_segments_on_side_stream(cuda, ora):
+    """20 000 triplets over 512 000 points: the fixed array of 2 097 152
+    partial sums allows only 104 segments where the length alone would ask
+    for 125, so the cap decides the split.  Run on a non-default stream,
+    twice, and compare a sample of triplets with the oracle's sums."""
+    torch, bsp = cuda
+    npts, nfields, ntrip = 80 ** 3, 12, 20000
+    rng = np.random.Generator(np.random.PCG64(77))
+    host = rng.standard_normal((nfields, npts)).astype(np.float32)
+    trip = rng.integers(0, nfields, size=(ntrip, 3)).astype(np.int32)
+    assert (npts + 4095) // 4096 > (1 << 21) // ntrip
+    fields = torch.from_numpy(host).cuda()
+    side = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            T = torch.full((ntrip,), float("nan"), dtype=torch.float64, device="cuda")
+            bsp.bsp_triple_sums_static(fields, npts, nfields, trip, T, stream=side)
+            outs.append(T)
+    side.synchronize()
+    outs = [t.cpu().numpy() for t in outs]
+    pick = rng.choice(ntrip, size=64, replace=False)
+    T_ora, _ = ora.sum3(list(host.astype(np.float64)), trip[pick])
+    # random fields: the sums cancel to ~sqrt(npts), so gate on the scale of the summands
+    scale = np.sqrt(npts) * np.ones_like(T_ora)
+    for got in outs:
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got[pick] - T_ora) / np.maximum(np.abs(T_ora), scale)) <= 1e-5
+    assert np.array_equal(outs[0], outs[1])
