@@ -77,7 +77,8 @@ typedef enum {
 
 /* Plan flags. */
 enum {
-    BSP_SHOT_NOISE = 1u   /* reserve workspace for Poisson shot-noise subtraction (BSP_FP32 only) */
+    BSP_SHOT_NOISE = 1u,  /* reserve workspace for Poisson shot-noise subtraction (BSP_FP32 only) */
+    BSP_FULL_TENSOR = 2u  /* output T^l[a; b >= c] for every a, not only the largest shell (see below) */
 };
 
 typedef struct bsp_plan bsp_plan;
@@ -91,7 +92,16 @@ typedef struct bsp_plan bsp_plan;
  *   n_ell    1..3 entries of ells, each in {0, 2, 4}, strictly ascending
  *            (odd l vanish by parity, Sec. 3.5).
  *   prec     a bsp_precision.
- *   flags    0 or BSP_SHOT_NOISE (triples the field workspace; BSP_FP32 only).
+ *   flags    0, BSP_SHOT_NOISE (triples the field workspace; BSP_FP32 only),
+ *            BSP_FULL_TENSOR, or both.
+ * The paper puts the Legendre weight on the largest side (Sec. 3.1, "with
+ * respect to the largest side"), so by default the bins are (a, b, c) with
+ * a >= b >= c and the weight on a.  With BSP_FULL_TENSOR the output bins are
+ * every distinct (a; b, c), b >= c, whose three shells form a valid bin, with
+ * the weight on a whichever shell it is: a < b puts L_l on a smaller side,
+ * so conventions that weight another leg (e.g. the first index of
+ * T^l[i, j, k]) can be read off.  For l = 0 the extra entries repeat the
+ * sorted bin's value.  Counts are those of the sorted bin.
  * Host-only: allocates the plan's small device tables on the current device.
  */
 bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells,
@@ -158,12 +168,16 @@ bsp_status bsp_modal_project(int n_keep, const double* gamma, int n_rhs, const d
  * bsp_batch_workspace_size: device workspace for prepare and run (one plan
  *   workspace shared by all sizes, two input buffers, a B staging area).
  * bsp_batch_prepare: counts for every size (BSP_EINVAL if the sizes disagree
- *   on the valid bins: rows would not line up); with autotune != 0 times
- *   the contraction grid {1024, 2048, 4096} x FFT batch {4, 16, 64} per
- *   size and keeps the fastest; then captures bsp_compute into one CUDA
- *   graph per (size, input buffer).  Synchronises `stream`.
- * bsp_batch_info / bsp_batch_bins: n_bins, the autotuner's choices and times
- *   (arrays of n_sizes), and the common bins / counts.
+ *   on the valid bins: rows would not line up); with autotune != 0 times,
+ *   per size, the FFT batch {4, 16, 64} against the CUDA-core contraction
+ *   grid {1024, 2048, 4096} (BSP_FP32) or the tensor-core tile height
+ *   {96, 64} x accumulation chunk {256, 128} points (bsp_plan_tune_tc;
+ *   never a chunk longer than the default) and keeps the fastest; then
+ *   captures bsp_compute into one CUDA graph per (size, input buffer).
+ *   Synchronises `stream`.
+ * bsp_batch_info / bsp_batch_tuning / bsp_batch_bins: n_bins, the
+ *   autotuner's choices and times (arrays of n_sizes; 0 = not tuned), and
+ *   the common bins / counts.
  * bsp_batch_run: for m < n_mocks, copies the complex64 half spectrum at host
  *   pointer delta_host[m] (pinned memory for overlap) of grid
  *   sizes[size_index[m]] into an input buffer on an internal copy stream while
@@ -183,6 +197,7 @@ bsp_status bsp_batch_workspace_size(const bsp_batch* batch, size_t* bytes);
 bsp_status bsp_batch_prepare(bsp_batch* batch, void* ws, void* stream, int autotune);
 bsp_status bsp_batch_info(const bsp_batch* batch, int* n_bins, int* tuned_ctas, int* tuned_fb,
                           double* tuned_ms);
+bsp_status bsp_batch_tuning(const bsp_batch* batch, int* max_rows, int* chunk_points);
 bsp_status bsp_batch_bins(const bsp_batch* batch, int32_t* abc, double* counts);
 bsp_status bsp_batch_run(bsp_batch* batch, int n_mocks, const int* size_index, const void* const* delta_host,
                          void* ws, void* stream, double* rows);
@@ -208,16 +223,17 @@ bsp_status bsp_counts(bsp_plan* plan, void* ws, void* stream);
 
 /*
  * Copy the counts and valid bins of `src` (after its bsp_counts) into `dst`,
- * a plan of the same grid and shells (any multipoles or precision), instead
- * of counting again.  Host-side plus small uploads; BSP_EINVAL if the
+ * a plan of the same grid and shells (any multipoles, precision or
+ * BSP_FULL_TENSOR setting), instead of counting again.  Host-side plus small uploads; BSP_EINVAL if the
  * geometries differ, BSP_ESTATE if src has no counts.
  */
 bsp_status bsp_plan_share_counts(bsp_plan* dst, const bsp_plan* src);
 
 /*
- * The valid bins after bsp_counts: *n_bins always; if abc != NULL the
- * bins as int32 [n_bins][3] (a, b, c); if counts != NULL the FP64 counts
- * [n_bins].  BSP_ESTATE before bsp_counts.
+ * The output bins after bsp_counts: *n_bins always; if abc != NULL the
+ * bins as int32 [n_bins][3] (a, b, c), lexicographic (a >= b >= c, or with
+ * BSP_FULL_TENSOR every (a; b >= c) described at bsp_plan_create); if
+ * counts != NULL the FP64 counts [n_bins].  BSP_ESTATE before bsp_counts.
  */
 bsp_status bsp_plan_bins(const bsp_plan* plan, int* n_bins, int32_t* abc, double* counts);
 
@@ -374,12 +390,36 @@ bsp_status bsp_plan_stats(const bsp_plan* plan, double* st);
 bsp_status bsp_plan_tune(bsp_plan* plan, int target_ctas, int fft_batch);
 
 /*
+ * Tensor-core schedule knobs (the batch runner's autotuner sets them):
+ * max_rows caps the MMA N of a work item (field rows per tile: 32 .. 96, a
+ * multiple of 8; 0 = keep; default 96): smaller works mean more, cheaper
+ * work items over the same pairs; chunk_points as for
+ * bsp_set_accumulation_chunk (0 = keep).  BSP_EUNSUPPORTED on a CUDA-core
+ * plan when a knob is set.  Standard plans rebuild their schedule at once
+ * when counts exist.
+ */
+bsp_status bsp_plan_tune_tc(bsp_plan* plan, int max_rows, int chunk_points);
+
+/*
  * Tensor-core paths only: the number of x-points (a multiple of 64, 64 ..
  * 2^20; default 256) summed in an FP32 tensor-memory accumulator before it
  * is folded into the compensated running sums.  Shorter chunks are more
  * accurate and cost more epilogue work.
  */
 bsp_status bsp_set_accumulation_chunk(bsp_plan* plan, int points);
+
+/*
+ * Tensor-core paths only: the limit, in SM clock cycles, of every wait
+ * inside the contraction's pipeline (copies landed, products written, MMAs
+ * done, accumulator drained, the pacing counter); 0 restores the default
+ * (2^33 cycles, about 4 s).  A wait that runs out makes the kernel record
+ * the error in the plan's error word (bsp_device_status), stop issuing work,
+ * wait for its own copies and MMAs in flight (always with the default limit)
+ * and release its tensor memory; the call's outputs are then undefined.
+ * For failure-path testing: a limit of a few hundred cycles makes the first
+ * wait for a copy run out.  1 <= cycles <= 2^40, or 0.
+ */
+bsp_status bsp_set_wait_limit(bsp_plan* plan, long long cycles);
 
 /*
  * Error word of the plan's kernels: 0 if no kernel has reported a problem,
@@ -439,6 +479,19 @@ bsp_status bsp_phase_times(bsp_plan* plan, double* ms, int* ncalls, int* launche
  */
 bsp_status bsp_triple_sums_static(const float* fields, size_t npts, int nfields,
                                   const int32_t* triplets, int ntrip, double* T, void* stream);
+
+/*
+ * Measured FP32 CUDA-core throughput of the current GPU (no counterpart in
+ * the paper; the peak the BSP_FP32 contraction's roofline is quoted
+ * against).  One block of 1024 threads per SM, 8 independent FMA chains per
+ * thread, `iters` FMAs per chain (a multiple of 16, >= 16); a short warm-up
+ * launch, then one launch timed with CUDA events on `stream`.
+ *   scratch  device float [n_SM * 1024], overwritten (4-byte aligned).
+ *   tflops   host, 2 * FMAs / time in TFLOP/s (out); ms host, the timed
+ *            launch's milliseconds (out, may be NULL).
+ * Synchronises `stream`.
+ */
+bsp_status bsp_fp32_fma_peak(int iters, void* stream, float* scratch, double* tflops, double* ms);
 
 /* Human-readable text for a status, and the last CUDA error text seen by
  * this thread ("" if none). */

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbsp.so")
 BSP_OK, BSP_EINVAL, BSP_ENOMEM, BSP_ECUDA, BSP_EUNSUPPORTED, BSP_ETIMEOUT, BSP_ESTATE = 0, -1, -2, -3, -4, -5, -6
 BSP_FP32, BSP_SPLIT_BF16, BSP_BF16, BSP_SPLIT_F16 = 0, 1, 2, 3
 BSP_SHOT_NOISE = 1
+BSP_FULL_TENSOR = 2
 PRECISIONS = {"fp32": BSP_FP32, "split_bf16": BSP_SPLIT_BF16, "bf16": BSP_BF16, "split_f16": BSP_SPLIT_F16}
 
 # (name, restype, argtypes) of every exported entry point declared in include/bsp.h
@@ -44,6 +45,10 @@ _SIGS = [
     ("bsp_host_staging_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("bsp_counts", ctypes.c_int, [_P, _P, _P]),
     ("bsp_plan_bins", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P, _P]),
+    ("bsp_set_wait_limit", ctypes.c_int, [_P, ctypes.c_longlong]),
+    ("bsp_plan_tune_tc", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    ("bsp_batch_tuning", ctypes.c_int, [_P, _P, _P]),
+    ("bsp_fp32_fma_peak", ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P]),
     ("bsp_bins_aliased", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     ("bsp_plan_share_counts", ctypes.c_int, [_P, _P]),
     ("bsp_compute", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P]),
@@ -305,6 +310,26 @@ def bsp_set_accumulation_chunk(plan: int, points: int):
     _check(load().bsp_set_accumulation_chunk(plan, int(points)), "bsp_set_accumulation_chunk")
 
 
+def bsp_plan_tune_tc(plan: int, max_rows: int = 0, chunk_points: int = 0):
+    _check(load().bsp_plan_tune_tc(plan, int(max_rows), int(chunk_points)), "bsp_plan_tune_tc")
+
+
+def bsp_set_wait_limit(plan: int, cycles: int):
+    _check(load().bsp_set_wait_limit(plan, int(cycles)), "bsp_set_wait_limit")
+
+
+def bsp_fp32_fma_peak(iters: int = 1 << 21, stream=None):
+    """(TFLOP/s, ms) of the library's FP32 FMA throughput kernel on the current GPU."""
+    import torch
+
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    scratch = torch.empty(nsm * 1024, dtype=torch.float32, device="cuda")
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().bsp_fp32_fma_peak(int(iters), _stream_handle(stream), _dptr(scratch), ctypes.byref(tf),
+                                    ctypes.byref(ms)), "bsp_fp32_fma_peak")
+    return tf.value, ms.value
+
+
 def bsp_set_profiling(plan: int, on: bool):
     _check(load().bsp_set_profiling(plan, int(bool(on))), "bsp_set_profiling")
 
@@ -360,7 +385,11 @@ class Batch:
         _check(lib.bsp_batch_info(self.h, ctypes.byref(nb), ctas.ctypes.data, fb.ctypes.data, ms.ctypes.data),
                "bsp_batch_info")
         self.nbins = nb.value
-        self.tuning = {"target_ctas": ctas.tolist(), "fft_batch": fb.tolist(), "ms": ms.tolist()}
+        rows_t = np.zeros(len(self.sizes), dtype=np.int32)
+        chunk_t = np.zeros(len(self.sizes), dtype=np.int32)
+        _check(lib.bsp_batch_tuning(self.h, rows_t.ctypes.data, chunk_t.ctypes.data), "bsp_batch_tuning")
+        self.tuning = {"target_ctas": ctas.tolist(), "fft_batch": fb.tolist(), "tc_max_rows": rows_t.tolist(),
+                       "tc_chunk_points": chunk_t.tolist(), "ms": ms.tolist()}
         self.bins = np.zeros((self.nbins, 3), dtype=np.int32)
         self.counts = np.zeros(self.nbins)
         _check(lib.bsp_batch_bins(self.h, self.bins.ctypes.data, self.counts.ctypes.data), "bsp_batch_bins")
@@ -492,13 +521,13 @@ class Bispectrum(Spectra):
     device) for a complex64 [n][n][n/2+1] CUDA tensor."""
 
     def __init__(self, n, box, edges, ells=(0, 2, 4), prec="fp32", host_staging=False, stream=None,
-                 counts_from=None, ws=None, shot_noise=False):
+                 counts_from=None, ws=None, shot_noise=False, full_tensor=False):
         import torch
 
         self.n, self.box, self.ells = int(n), float(box), tuple(ells)
         self.edges = [float(e) for e in edges]
         self.plan = bsp_plan_create(n, box, edges, ells, PRECISIONS.get(prec, prec),
-                                    BSP_SHOT_NOISE if shot_noise else 0)
+                                    (BSP_SHOT_NOISE if shot_noise else 0) | (BSP_FULL_TENSOR if full_tensor else 0))
         nbytes = bsp_workspace_size(self.plan)
         if host_staging:
             nbytes += bsp_host_staging_size(self.plan)

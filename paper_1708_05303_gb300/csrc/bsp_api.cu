@@ -83,6 +83,20 @@ struct HostSched {
 
 typedef std::vector<std::array<int, 3>> BinList;
 
+// Every distinct (a; b >= c) whose shells form one of the sorted bins, in
+// lexicographic order: the Legendre leg on each of the three shells in turn.
+BinList expand_full(const BinList& sorted) {
+    std::map<std::array<int, 3>, int> m;
+    for (const auto& t : sorted)
+        for (int k = 0; k < 3; ++k) {
+            const int a = t[k], u = t[(k + 1) % 3], v = t[(k + 2) % 3];
+            m[{a, std::max(u, v), std::min(u, v)}] = 1;
+        }
+    BinList out;
+    for (auto& kv : m) out.push_back(kv.first);
+    return out;
+}
+
 // Tiles of <= `cols` pairs (b, c) (sorted by b, then c; the shells they touch
 // span <= 64), each with the rows (slot, a) for a in the tile's a-range, cut
 // into chunks of <= 64 rows.
@@ -241,7 +255,8 @@ void assign_units(TcSched& h, size_t npts, int nsm) {
 
 // Fields are numbered slot * pad + a (pad = nsh rounded up to 8) so that
 // every box of 8 fields is one group of the K-block-major 16-bit planes.
-TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, int pad, size_t npts, int nsm) {
+TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, int pad, size_t npts, int nsm,
+                       int max_boxes = 12) {
     TcSched h;
     // a-range of each pair (b, c) over the bins, in groups of 8 shells
     std::map<std::pair<int, int>, std::pair<int, int>> arange;
@@ -285,9 +300,10 @@ TcSched build_tc_sched(const BinList& bins, const std::vector<int>& out_slots, i
         std::vector<int> boxes;
         for (int si : out_slots)
             for (int g = 0; g < nbs; ++g) boxes.push_back(si * pad + 8 * (glo + g));
-        // works of at most 12 boxes (N <= 96), split evenly
+        // works of at most max_boxes boxes (N <= 8 max_boxes, <= 96), split evenly
         const int work0 = (int)h.works.size();
-        const int nwk = ((int)boxes.size() + 11) / 12, per = ((int)boxes.size() + nwk - 1) / nwk;
+        const int nwk = ((int)boxes.size() + max_boxes - 1) / max_boxes;
+        const int per = ((int)boxes.size() + nwk - 1) / nwk;
         for (size_t b0 = 0; b0 < boxes.size(); b0 += per) {
             TcWork w{};
             w.pair0 = (int)i;
@@ -350,6 +366,7 @@ struct bsp_plan {
     cx<double>* d_tw64 = nullptr;
     FieldDesc* d_fd_delta = nullptr;  // [nslot*nsh], or [3][nslot*nsh] with shot noise
     bool shot = false;                // BSP_SHOT_NOISE: workspace for the shot-noise fields
+    bool full = false;                // BSP_FULL_TENSOR: the Legendre leg on every shell of a bin
     // modal plans (Sec. 3.5): fields M^l_p from radial tables, all (a; b >= c) sums
     bool modal = false;
     int slot2 = -1;                   // slot of l = 2 (the U term of l = 4), or -1
@@ -368,10 +385,17 @@ struct bsp_plan {
     BinList cand;
     HostSched cand_sched;
     DevSched cand_dev;
+    // counts on the fundamental domain of the cubic group: representative
+    // points (linear index) and their orbit sizes
+    uint32_t* d_rep_idx = nullptr;
+    double* d_rep_w = nullptr;
+    size_t nrep = 0;
     // valid bins after counts
     bool have_counts = false;
-    BinList bins;
+    BinList bins;                     // output bins (a; b >= c), the Legendre leg a
     std::vector<double> counts;
+    BinList vbins;                    // valid sorted bins a >= b >= c and their counts
+    std::vector<double> vcounts;
     double* d_counts = nullptr;
     HostSched comp_sched;
     DevSched comp_dev;
@@ -389,6 +413,8 @@ struct bsp_plan {
     int* d_err = nullptr;
     unsigned* d_fmax = nullptr;   // per-field magnitude bounds for the 16-bit scaling
     int chunk_kb = 4;             // K-blocks (64 points each) per FP32 tensor-memory accumulation
+    long long wait_cycles = 0;    // tensor-core pipeline wait limit in clock cycles (0: the kernel's default)
+    int tc_max_boxes = 12;        // tensor-core works: at most this many boxes of 8 field rows (N <= 8 x this)
     size_t f0_bytes = 0, plane_bytes = 0, tc_part_bytes = 0;
     // workspace layout
     size_t fld32_bytes = 0, fld64_bytes = 0, t12_bytes32 = 0, t12_bytes64 = 0;
@@ -405,6 +431,7 @@ struct bsp_plan {
         for (auto e : ev_pool) cudaEventDestroy(e);
         cudaFree(d_shell_of); cudaFree(d_tw32); cudaFree(d_tw64); cudaFree(d_fd_raw); cudaFree(d_shell_sub);
         cudaFree(d_fd_delta); cudaFree(d_fd_unit); cudaFree(d_counts);
+        cudaFree(d_rep_idx); cudaFree(d_rep_w);
         cudaFree(d_fd_tc); cudaFree(d_tc_works); cudaFree(d_tc_pairs); cudaFree(d_tc_loc); cudaFree(d_err);
         cudaFree(d_fmax);
         cudaFree(d_tc_units); cudaFree(d_tcu_units);
@@ -473,11 +500,35 @@ Layout layout_counts(const bsp_plan* p) {
     L.fields = 0;
     L.t1 = L.fields + p->fld64_bytes;
     L.t2 = L.t1 + t1 * p->fb64;
-    L.partial = L.t2 + t2 * p->fb64;
+    // the unit fields gathered on the representative points, weighted and
+    // unweighted ([n_shells][nrep] FP64 each), then the partial sums
+    L.partial = L.t2 + t2 * p->fb64 + 2 * round256((size_t)p->nsh * p->nrep * sizeof(double));
     L.tout = L.partial + round256(partial_bytes(p->cand_sched, CCOLS));
     L.cnt = L.tout;
     L.end = L.cnt + p->cnt_out_bytes;
     return L;
+}
+
+// Representatives of the orbits of the cubic group (axis permutations and
+// sign flips, x -> n - x per axis) on the n^3 grid: 0 <= x <= y <= z <= n/2,
+// with the orbit size (distinct permutations of (x, y, z) times 2 for every
+// coordinate other than 0 and n/2).  A shell's unit field I_a(x) =
+// sum_{m in a} cos(2 pi m.x / n) is invariant under the group (the shell
+// depends on |m|^2 only), so sum_x I_a I_b I_c = sum_reps w I_a I_b I_c.
+void cubic_reps(int n, std::vector<uint32_t>& idx, std::vector<double>& w) {
+    const int h = n / 2;
+    idx.clear();
+    w.clear();
+    for (int x = 0; x <= h; ++x)
+        for (int y = x; y <= h; ++y)
+            for (int z = y; z <= h; ++z) {
+                const int perms = (x == y && y == z) ? 1 : (x == y || y == z) ? 3 : 6;
+                int flips = 1;
+                for (int v : {x, y, z})
+                    if (v != 0 && v != h) flips *= 2;
+                idx.push_back((uint32_t)(((size_t)x * n + y) * n + z));
+                w.push_back((double)(perms * flips));
+            }
 }
 
 bool good_size(int n) {
@@ -514,7 +565,7 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     if (!out) return BSP_EINVAL;
     *out = nullptr;
     if (!good_size(n) || !(box > 0) || !std::isfinite(box) || n_shells < 1 || n_shells > 64 || !edges_kf ||
-        n_ell < 1 || n_ell > 3 || !ells || (flags & ~(unsigned)BSP_SHOT_NOISE))
+        n_ell < 1 || n_ell > 3 || !ells || (flags & ~(unsigned)(BSP_SHOT_NOISE | BSP_FULL_TENSOR)))
         return BSP_EINVAL;
     for (int i = 0; i <= n_shells; ++i)
         if (!(edges_kf[i] > 0) || !std::isfinite(edges_kf[i]) || (i && !(edges_kf[i] > edges_kf[i - 1])))
@@ -543,6 +594,7 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
             p->nsm = sms;
     }
     p->shot = (flags & BSP_SHOT_NOISE) != 0;
+    p->full = (flags & BSP_FULL_TENSOR) != 0;
     p->tc = prec != BSP_FP32;
     p->nprod = prec == BSP_BF16 ? 1 : 3;
     p->slot_ell.push_back(0);
@@ -626,13 +678,24 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
                 if (e[a] < e[b + 1] + e[c + 1] || e[a + 1] + e[b + 1] + e[c + 1] > n)
                     p->cand.push_back({a, b, c});
             }
-    p->cand_sched = build_sched(p->cand, std::vector<int>{0}, n_shells, p->npts(), p->target_ctas, CCOLS);
+    {
+        std::vector<uint32_t> ridx;
+        std::vector<double> rw;
+        cubic_reps(n, ridx, rw);
+        p->nrep = ridx.size();
+        if ((st = upload(&p->d_rep_idx, ridx)) != BSP_OK || (st = upload(&p->d_rep_w, rw)) != BSP_OK) {
+            delete p;
+            return st;
+        }
+    }
+    p->cand_sched = build_sched(p->cand, std::vector<int>{0}, n_shells, p->nrep, p->target_ctas, CCOLS);
     if ((st = upload_sched(p->cand_dev, p->cand_sched)) != BSP_OK) {
         delete p;
         return st;
     }
-    // workspace sizing: compute schedule bounded by the candidate bins
-    HostSched bound = build_sched(p->cand, p->out_slots, n_shells, p->npts(), p->target_ctas, CCOLS);
+    // workspace sizing: compute schedule bounded by the candidate output bins
+    const BinList ocand = p->full ? expand_full(p->cand) : p->cand;
+    HostSched bound = build_sched(ocand, p->out_slots, n_shells, p->npts(), p->target_ctas, CCOLS);
     size_t t1, t2;
     t12_sizes(g, sizeof(float), &t1, &t2);
     const size_t nfields32 = (size_t)p->nslot() * n_shells;
@@ -647,12 +710,13 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     p->part_bytes = round256(std::max(partial_bytes(bound, CCOLS),
                                       (size_t)(4096 + bound.works.size()) * 64 * CCOLS * sizeof(double)));
     if (p->shot) p->part_bytes *= 4;   // main sum + three shot-noise sums
-    p->tout_bytes = round256(p->ells.size() * p->cand.size() * sizeof(double));
+    p->tout_bytes = round256(p->ells.size() * ocand.size() * sizeof(double));
     if (p->tc) {
         p->kb_rows32 = n_shells;
         p->f0_bytes = round256((size_t)n_shells * p->nkb() * 256);
         p->plane_bytes = round256((size_t)p->groups16 * p->nkb() * 1024);   // hi and lo: 2 * plane_bytes
-        TcSched tb = build_tc_sched(p->cand, p->out_slots, pad16, p->npts(), p->nsm);
+        // partial slots for the most works any tuning can make (works of 4 boxes)
+        TcSched tb = build_tc_sched(ocand, p->out_slots, pad16, p->npts(), p->nsm, 4);
         p->tc_part_bytes = round256(std::max<size_t>((size_t)p->nsm, tb.units.size()) * TC_UNIT * sizeof(double));
     }
     p->cnt_out_bytes = round256(p->cand.size() * sizeof(double));
@@ -851,13 +915,33 @@ bsp_status bsp_host_staging_size(const bsp_plan* p, size_t* bytes) {
 
 // After the valid bins and counts are known: contraction schedules and the
 // device copy of the counts.
+// Output bins from the valid sorted bins: the sorted list itself, or with
+// BSP_FULL_TENSOR every distinct (a; b >= c) whose shells are a valid sorted
+// bin, lexicographic, each with that bin's count.
+static void set_output_bins(bsp_plan* p) {
+    if (!p->full) {
+        p->bins = p->vbins;
+        p->counts = p->vcounts;
+        return;
+    }
+    std::map<std::array<int, 3>, double> cnt;   // sorted shells -> count
+    for (size_t i = 0; i < p->vbins.size(); ++i) cnt[p->vbins[i]] = p->vcounts[i];
+    p->bins = expand_full(p->vbins);
+    p->counts.clear();
+    for (const auto& t : p->bins) {
+        std::array<int, 3> s = t;
+        std::sort(s.begin(), s.end(), [](int x, int y) { return x > y; });
+        p->counts.push_back(cnt[s]);
+    }
+}
+
 static bsp_status finish_counts(bsp_plan* p) {
     p->comp_sched = build_sched(p->bins, p->out_slots, p->nsh, p->npts(), p->target_ctas, CCOLS);
     if (round256(partial_bytes(p->comp_sched, CCOLS)) * (p->shot ? 4 : 1) > p->part_bytes) return BSP_ENOMEM;
     bsp_status s = upload_sched(p->comp_dev, p->comp_sched);
     if (s != BSP_OK) return s;
     if (p->tc) {
-        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->pad16, p->npts(), p->nsm);
+        p->tc_sched = build_tc_sched(p->bins, p->out_slots, p->pad16, p->npts(), p->nsm, p->tc_max_boxes);
         if (round256(p->tc_sched.units.size() * TC_UNIT * sizeof(double)) > p->tc_part_bytes) return BSP_ENOMEM;
         cudaFree(p->d_tc_works); cudaFree(p->d_tc_pairs); cudaFree(p->d_tc_loc); cudaFree(p->d_tc_units);
         p->d_tc_works = nullptr; p->d_tc_pairs = nullptr; p->d_tc_loc = nullptr; p->d_tc_units = nullptr;
@@ -891,11 +975,17 @@ bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
                                                   nullptr, st);
         if (e != cudaSuccess) return cuda_fail(e, "fft (counts)");
     }
+    // gather the unit fields on the representatives of the cubic group's
+    // orbits (weighted rows, unweighted pair factors), then contract there
+    const size_t cbytes = round256((size_t)p->nsh * p->nrep * sizeof(double));
+    double* wrows = (double*)(base + L.partial - 2 * cbytes);
+    double* urows = (double*)(base + L.partial - cbytes);
+    cudaError_t e = launch_gather_reps(f64, p->npts(), p->nsh, p->d_rep_idx, p->d_rep_w, p->nrep, wrows, urows, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gather (counts)");
     double* partial = (double*)(base + L.partial);
     double* cnt = (double*)(base + L.cnt);
-    cudaError_t e = launch_contract_cc<double>(f64, f64, nullptr, 0, p->npts(), p->cand_dev.works, p->cand_dev.nwork,
-                                               p->cand_dev.pairs, p->cand_dev.rowf, p->npts(),
-                                               p->cand_dev.nsplit, partial, st);
+    e = launch_contract_cc<double>(wrows, urows, nullptr, 0, p->nrep, p->cand_dev.works, p->cand_dev.nwork,
+                                   p->cand_dev.pairs, p->cand_dev.rowf, p->nrep, p->cand_dev.nsplit, partial, st);
     if (e != cudaSuccess) return cuda_fail(e, "contract (counts)");
     const double n3 = (double)p->npts();
     e = launch_reduce(partial, p->cand_dev.nsplit, 0, 0, p->cand_dev.loc, (int)p->cand.size(),
@@ -904,13 +994,14 @@ bsp_status bsp_counts(bsp_plan* p, void* ws, void* stream) {
     std::vector<double> hc(p->cand.size());
     CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(double) * hc.size(), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    p->bins.clear();
-    p->counts.clear();
+    p->vbins.clear();
+    p->vcounts.clear();
     for (size_t i = 0; i < p->cand.size(); ++i)
         if (hc[i] >= 1.0) {
-            p->bins.push_back(p->cand[i]);
-            p->counts.push_back(hc[i]);
+            p->vbins.push_back(p->cand[i]);
+            p->vcounts.push_back(hc[i]);
         }
+    set_output_bins(p);
     return finish_counts(p);
 }
 
@@ -918,8 +1009,9 @@ bsp_status bsp_plan_share_counts(bsp_plan* dst, const bsp_plan* src) {
     if (!dst || !src || dst == src) return BSP_EINVAL;
     if (!src->have_counts) return BSP_ESTATE;
     if (dst->n != src->n || dst->nsh != src->nsh || dst->edges != src->edges) return BSP_EINVAL;
-    dst->bins = src->bins;
-    dst->counts = src->counts;
+    dst->vbins = src->vbins;
+    dst->vcounts = src->vcounts;
+    set_output_bins(dst);
     return finish_counts(dst);
 }
 
@@ -1011,7 +1103,7 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
                                            p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
-                                           p->chunk_kb, partial, p->d_err, (unsigned*)p->d_err + 1, st);
+                                           p->chunk_kb, partial, p->d_err, (unsigned*)p->d_err + 1, st, p->wait_cycles);
         if (e != cudaSuccess) return cuda_fail(e, "contract (tensor cores)");
         if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
         const double V = p->box * p->box * p->box;
@@ -1157,7 +1249,7 @@ bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* s
                                            p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
-                                           p->chunk_kb, part, p->d_err, (unsigned*)p->d_err + 1, st);
+                                           p->chunk_kb, part, p->d_err, (unsigned*)p->d_err + 1, st, p->wait_cycles);
         if (e != cudaSuccess) return cuda_fail(e, "contract (modal, tensor cores)");
         ++launches;
         if (p->need_u) {
@@ -1165,7 +1257,7 @@ bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* s
                                    p->d_tcu_works, p->d_tcu_units,
                                    (int)p->tc_u_sched.units.size(), p->tc_u_sched.lsup, p->tc_u_sched.nsup,
                                    p->d_tcu_pairs, p->slot2 * p->pad16, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
-                                   p->chunk_kb, upart, p->d_err, (unsigned*)p->d_err + 2, st);
+                                   p->chunk_kb, upart, p->d_err, (unsigned*)p->d_err + 2, st, p->wait_cycles);
             if (e != cudaSuccess) return cuda_fail(e, "contract (modal U, tensor cores)");
             ++launches;
         }
@@ -1250,9 +1342,28 @@ bsp_status bsp_plan_tune(bsp_plan* p, int target_ctas, int fft_batch) {
     return BSP_OK;
 }
 
+bsp_status bsp_plan_tune_tc(bsp_plan* p, int max_rows, int chunk_points) {
+    if (!p || (max_rows && (max_rows < 32 || max_rows > 96 || max_rows % 8)) ||
+        (chunk_points && (chunk_points < 64 || chunk_points % 64 || chunk_points > (1 << 20))))
+        return BSP_EINVAL;
+    if (!p->tc) return max_rows || chunk_points ? BSP_EUNSUPPORTED : BSP_OK;
+    if (chunk_points) p->chunk_kb = chunk_points / 64;
+    if (max_rows && max_rows / 8 != p->tc_max_boxes) {
+        p->tc_max_boxes = max_rows / 8;
+        if (p->have_counts && !p->modal) return finish_counts(p);
+    }
+    return BSP_OK;
+}
+
 bsp_status bsp_set_accumulation_chunk(bsp_plan* p, int points) {
     if (!p || points < 64 || points % 64 || points > (1 << 20)) return BSP_EINVAL;
     p->chunk_kb = points / 64;
+    return BSP_OK;
+}
+
+bsp_status bsp_set_wait_limit(bsp_plan* p, long long cycles) {
+    if (!p || cycles < 0 || cycles > (1ll << 40)) return BSP_EINVAL;
+    p->wait_cycles = cycles;
     return BSP_OK;
 }
 

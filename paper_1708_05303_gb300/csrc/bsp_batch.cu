@@ -85,7 +85,9 @@ struct bsp_batch {
     cudaGraphExec_t exec[MAX_SIZES][2] = {{nullptr}};
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
+    int prec = 0;
     int tuned_ctas[MAX_SIZES] = {0}, tuned_fb[MAX_SIZES] = {0};
+    int tuned_rows[MAX_SIZES] = {0}, tuned_chunk[MAX_SIZES] = {0};   // tensor-core plans
     double tuned_ms[MAX_SIZES] = {0};
     ~bsp_batch() {
         for (int s = 0; s < nsizes; ++s) {
@@ -117,6 +119,7 @@ bsp_status bsp_batch_create(bsp_batch** out, int n_sizes, const int* sizes, doub
     bsp_batch* bt = new (std::nothrow) bsp_batch();
     if (!bt) return BSP_ENOMEM;
     bt->n_ell = n_ell;
+    bt->prec = prec;
     for (int s = 0; s < n_sizes; ++s) {
         bsp_status st = bsp_plan_create(&bt->plans[s], sizes[s], box, n_shells, edges_kf, n_ell, ells, prec, 0);
         if (st != BSP_OK) {
@@ -166,17 +169,32 @@ bsp_status bsp_batch_prepare(bsp_batch* bt, void* ws, void* stream, int autotune
     if ((size_t)bt->n_ell * bt->nbins > (size_t)bt->n_ell * 45760) return BSP_EINVAL;
     double* Bst = b_stage(bt, ws);
     if (cudaMemsetAsync(in_buf(bt, ws, 0), 0, 2 * r256(bt->in_max), st) != cudaSuccess) return BSP_ECUDA;
-    // autotune: contraction grid target and FFT batch width, timed on the (zero) input
+    // autotune, timed on the (zero) input: the FFT batch width, and the
+    // contraction grid target (CUDA-core plans) or the tensor-core tile height
+    // and accumulation chunk (no chunk longer than the default 256 points, so
+    // the tuned schedule is never less accurate than the untuned one)
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BSP_ECUDA;
+    const bool tc = bt->prec != BSP_FP32;
     for (int s = 0; s < bt->nsizes; ++s) {
-        int best_c = 0, best_f = 0;
+        int best_c = 0, best_f = 0, best_r = 0, best_k = 0;
         double best = 1e30;
         const int ctas[] = {1024, 2048, 4096};
+        const int rows_opt[] = {96, 64};
+        const int chunk_opt[] = {256, 128};
         const int fbs[] = {4, 16, 64};
-        for (int ci = 0; ci < (autotune ? 3 : 1); ++ci)
+        const int na = autotune ? (tc ? 4 : 3) : 1;
+        for (int ai = 0; ai < na; ++ai)
             for (int fi = 0; fi < (autotune ? 3 : 1); ++fi) {
-                const int c = autotune ? ctas[ci] : 0, f = autotune ? fbs[fi] : 0;
+                const int f = autotune ? fbs[fi] : 0;
+                int c = 0, rw = 0, ck = 0;
+                if (autotune && tc) {
+                    rw = rows_opt[ai / 2];
+                    ck = chunk_opt[ai % 2];
+                    if (bsp_plan_tune_tc(bt->plans[s], rw, ck) != BSP_OK) continue;
+                } else if (autotune) {
+                    c = ctas[ai];
+                }
                 if (bsp_plan_tune(bt->plans[s], c, f) != BSP_OK) continue;
                 bsp_status r = BSP_OK;
                 for (int rep = 0; rep < 2 && r == BSP_OK; ++rep)   // warm-up, then timed
@@ -193,11 +211,16 @@ bsp_status bsp_batch_prepare(bsp_batch* bt, void* ws, void* stream, int autotune
                     best = ms;
                     best_c = c;
                     best_f = f;
+                    best_r = rw;
+                    best_k = ck;
                 }
             }
+        if (tc && autotune) bsp_plan_tune_tc(bt->plans[s], best_r, best_k);
         bsp_plan_tune(bt->plans[s], best_c, best_f);
         bt->tuned_ctas[s] = best_c;
         bt->tuned_fb[s] = best_f;
+        bt->tuned_rows[s] = best_r;
+        bt->tuned_chunk[s] = best_k;
         bt->tuned_ms[s] = best;
     }
     cudaEventDestroy(e0);
@@ -238,6 +261,16 @@ bsp_status bsp_batch_info(const bsp_batch* bt, int* n_bins, int* tuned_ctas, int
         if (tuned_ctas) tuned_ctas[s] = bt->tuned_ctas[s];
         if (tuned_fb) tuned_fb[s] = bt->tuned_fb[s];
         if (tuned_ms) tuned_ms[s] = bt->tuned_ms[s];
+    }
+    return BSP_OK;
+}
+
+bsp_status bsp_batch_tuning(const bsp_batch* bt, int* max_rows, int* chunk_points) {
+    if (!bt) return BSP_EINVAL;
+    if (!bt->prepared) return BSP_ESTATE;
+    for (int s = 0; s < bt->nsizes; ++s) {
+        if (max_rows) max_rows[s] = bt->tuned_rows[s];
+        if (chunk_points) chunk_points[s] = bt->tuned_chunk[s];
     }
     return BSP_OK;
 }

@@ -13,6 +13,8 @@
 // the block error, and written once to the CTA's own FP64 slot.  The reduction
 // sums the per-segment partials in a fixed order in FP64 (deterministic),
 // then normalises: B = T / (V n^3 N_abc) or N_abc = rint(T / n^3).
+#include <algorithm>
+
 #include "bsp_internal.h"
 
 namespace bsp {
@@ -200,7 +202,30 @@ __global__ void k_reduce(const double* __restrict__ partial, int nsplit, size_t 
     out[i] = v / counts[i % nbins];
 }
 
+// Unit fields on the orbit representatives: w_r I_a(x_r) and I_a(x_r) for
+// every shell a (grid-stride over a * nrep + r).
+__global__ void k_gather_reps(const double* __restrict__ fields, size_t npts, int nsh,
+                              const uint32_t* __restrict__ idx, const double* __restrict__ w, size_t nrep,
+                              double* __restrict__ wrows, double* __restrict__ urows) {
+    const size_t total = (size_t)nsh * nrep;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t a = i / nrep, r = i - a * nrep;
+        const double v = fields[a * npts + idx[r]];
+        urows[i] = v;
+        wrows[i] = v * w[r];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_gather_reps(const double* fields, size_t npts, int nsh, const uint32_t* idx, const double* w,
+                               size_t nrep, double* wrows, double* urows, cudaStream_t st) {
+    if (nsh <= 0 || nrep == 0) return cudaSuccess;
+    const size_t total = (size_t)nsh * nrep;
+    const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
+    k_gather_reps<<<blocks, 256, 0, st>>>(fields, npts, nsh, idx, w, nrep, wrows, urows);
+    return cudaGetLastError();
+}
 
 template <typename R>
 cudaError_t launch_contract_cc(const R* rows, const R* px, const R* py, int sym, size_t fstride, const Work* works,

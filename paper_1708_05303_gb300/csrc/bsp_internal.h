@@ -131,6 +131,11 @@ cudaError_t launch_contract_cc(const R* rows, const R* px, const R* py, int sym,
                                const int* row_fields, size_t npts, int nsplit, double* partial,
                                cudaStream_t st);
 
+// Counts on the cubic group's orbit representatives: wrows[a][r] = w[r] *
+// fields[a][idx[r]], urows[a][r] = fields[a][idx[r]] (FP64, [nsh][nrep]).
+cudaError_t launch_gather_reps(const double* fields, size_t npts, int nsh, const uint32_t* idx, const double* w,
+                               size_t nrep, double* wrows, double* urows, cudaStream_t st);
+
 cudaError_t launch_reduce(const double* partial, int nsplit, size_t unit, int row_stride,
                           const BinLoc* loc, int nout, int nbins, const double* counts, double scale,
                           int mode, double* T_out, double* out, cudaStream_t st,
@@ -145,7 +150,7 @@ cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_ro
                                int groups, long long nkb, const TcWork* works, const TcUnit* units, int nunits,
                                int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
-                               unsigned* pace, cudaStream_t st);
+                               unsigned* pace, cudaStream_t st, long long wait_cycles = 0);
 
 // ---- density input stage (bsp_fft.cu) ----
 struct DensityLayout {   // byte offsets in the caller's workspace

@@ -103,7 +103,7 @@ __device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit = WAIT_CYCLES) {
     const uint32_t addr = smem_u32(b);
     if (mbar_test(addr, parity)) return true;
     const long long t0 = clock64();
@@ -116,7 +116,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
             : "r"(addr), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -236,13 +236,13 @@ __device__ __forceinline__ void unpack64(uint64_t v, float& x0, float& x1) {
 }
 
 // Wait until *ctr >= target (acquire); false after ~4 s.
-__device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target) {
+__device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target, long long limit) {
     const long long t0 = clock64();
     while (true) {
         unsigned v;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
         if (v >= target) return true;
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
         __nanosleep(64);
     }
 }
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   const int2* __restrict__ pair_shells, int pair_base,
                   const unsigned* __restrict__ fmax2, float bound_mul, const TcUnit* __restrict__ units,
                   int lsup, int nsup, int nprod, int CHUNK, double* __restrict__ partial,
-                  int* __restrict__ err, unsigned* __restrict__ pace, int drift) {
+                  int* __restrict__ err, unsigned* __restrict__ pace, int drift, long long wlim) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int issued = 0;
             for (int k = 0; k < nkb && !S.abort; ++k) {
                 const int s = k % NT, u = k / NT;
-                if (u > 0 && !mbar_wait(&S.kb_done[s], (u - 1) & 1)) {
+                if (u > 0 && !mbar_wait(&S.kb_done[s], (u - 1) & 1, wlim)) {
                     set_abort(S, err, 1);
                     break;
                 }
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // pacing: super-segment sup starts once every CTA has issued the loads
                 // of super-segments < sup - drift, so that works whose K-blocks cost
                 // different times still read the same fields while they sit in L2
-                if (pace && kin == 0 && sup > drift && !wait_count(pace, (unsigned)(gridDim.x * (sup - drift)))) {
+                if (pace && kin == 0 && sup > drift && !wait_count(pace, (unsigned)(gridDim.x * (sup - drift)), wlim)) {
                     set_abort(S, err, 128);
                     break;
                 }
@@ -375,7 +375,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 issued = k + 1;
                 if (pace && kin == unit.len - 1) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(pace) : "memory");
             }
-            // copies in flight must land before the CTA can exit: the last use of each stage
+            // copies in flight must land before the CTA can exit: the last use of each
+            // stage (always the long limit, whatever the pipeline waits use)
             for (int k = max(0, issued - NT); k < issued; ++k)
                 if (!mbar_wait(&S.tma_full[k % NT], (k / NT) & 1)) atomicOr(err, 16);
         }
@@ -388,15 +389,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int s = k % NT, u = k / NT, sa = k & 1;
                 const int j = c & 1;
                 const bool efirst = kc == 0 && c % CC == 0;   // first K-block of a drain period of E
-                if (kc == 0 && c >= 2 && !mbar_wait(&S.acc_empty[j], ((c >> 1) - 1) & 1)) {
+                if (kc == 0 && c >= 2 && !mbar_wait(&S.acc_empty[j], ((c >> 1) - 1) & 1, wlim)) {
                     set_abort(S, err, 2);
                     break;
                 }
-                if (nprod == 3 && efirst && c > 0 && !mbar_wait(&S.corr_empty, ((c / CC) - 1) & 1)) {
+                if (nprod == 3 && efirst && c > 0 && !mbar_wait(&S.corr_empty, ((c / CC) - 1) & 1, wlim)) {
                     set_abort(S, err, 2);
                     break;
                 }
-                if (!mbar_wait(&S.tma_full[s], u & 1) || !mbar_wait(&S.a_full[sa], (k >> 1) & 1)) {
+                if (!mbar_wait(&S.tma_full[s], u & 1, wlim) || !mbar_wait(&S.a_full[sa], (k >> 1) & 1, wlim)) {
                     set_abort(S, err, 4);
                     break;
                 }
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 done = k + 1;
             }
-            // the last MMAs must finish before tensor memory is released
+            // the last MMAs must finish before tensor memory is released (long limit)
             if (done > 0 && !mbar_wait(&S.kb_done[(done - 1) % NT], ((done - 1) / NT) & 1)) atomicOr(err, 32);
         }
     } else if (warp >= W_PRO0 && warp < W_PRO0 + N_PRO) {
@@ -440,8 +441,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t lanebase = ((uint32_t)(32 * q) << 16) + (uint32_t)(t * PRO_PTS / 2);
         for (int k = 0; k < nkb && !S.abort; ++k) {
             const int s = k % NT, u = k / NT, sa = k & 1;
-            if (!mbar_wait(&S.tma_full[s], u & 1) ||
-                (k >= 2 && !mbar_wait(&S.kb_done[(k - 2) % NT], ((k - 2) / NT) & 1))) {
+            if (!mbar_wait(&S.tma_full[s], u & 1, wlim) ||
+                (k >= 2 && !mbar_wait(&S.kb_done[(k - 2) % NT], ((k - 2) / NT) & 1, wlim))) {
                 set_abort(S, err, 8);
                 break;
             }
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int c = 0; c < nch && !S.abort; ++c) {
             const int j = c & 1, g = c % FL;
             const bool flush = g == FL - 1 || c == nch - 1;
-            if (!mbar_wait(&S.acc_full[j], (c >> 1) & 1)) {
+            if (!mbar_wait(&S.acc_full[j], (c >> 1) & 1, wlim)) {
                 set_abort(S, err, 64);
                 break;
             }
@@ -565,8 +566,9 @@ cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_ro
                                int groups, long long nkb, const TcWork* works, const TcUnit* units, int nunits,
                                int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
-                               unsigned* pace, cudaStream_t st) {
+                               unsigned* pace, cudaStream_t st, long long wait_cycles) {
     const size_t smem = tc_smem_bytes();
+    const long long wlim = wait_cycles > 0 ? wait_cycles : WAIT_CYCLES;
     static bool set16 = false, setb = false;   // once per kernel, never inside a graph capture
     static int resident = -1;                  // CTAs that fit on the device at once
     auto kern = f16 ? k_contract_tc<true> : k_contract_tc<false>;
@@ -600,7 +602,7 @@ cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_ro
     cfg.numAttrs = 1;
     unsigned* pc = paced ? pace : nullptr;
     return cudaLaunchKernelEx(&cfg, kern, f0, f0_rows, f0_row0, planes, groups, nkb, works, pair_shells, pair_base, fmax2, bound_mul, units, lsup, nsup,
-                              nprod, chunk_kb, partial, err, pc, drift);
+                              nprod, chunk_kb, partial, err, pc, drift, wlim);
 }
 
 }  // namespace bsp

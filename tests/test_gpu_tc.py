@@ -98,3 +98,35 @@ def test_split_f16_close_to_fp32_path(torch_cuda):
     _, Btc, status = run(torch_cuda, dk, n, edges, (0, 2, 4), "split_f16", chunk=64)
     assert status == 0
     assert gate(Btc, B32) <= 2e-5
+
+
+def test_wait_limit_runs_out_and_the_plan_recovers(torch_cuda):
+    """Failure path of the bounded waits, without a GPU fault: with a pipeline
+    wait limit of 200 cycles the first wait for a copy runs out, the kernel
+    records it in the plan's error word and returns (the context stays
+    usable); with the default limit restored the same plan gives the same
+    bins bit for bit and a clear error word."""
+    from paper_1708_05303_gb300 import bsp
+
+    torch = torch_cuda
+    n, edges = 32, linear_edges(8)
+    dk, _ = make_field(FieldModel(n=n, box=BOX, sigma_g=0.3), 5)
+    d = torch.from_numpy(dk).cuda()
+    est = bsp.Bispectrum(n, BOX, edges, (0, 2, 4), prec="split_f16")
+    before = est.compute(d).clone()
+    torch.cuda.synchronize()
+    assert bsp.bsp_device_status(est.plan) == 0
+    bsp.bsp_set_wait_limit(est.plan, 200)
+    est.compute(d)
+    torch.cuda.synchronize()            # the kernel returned; no CUDA error
+    code = bsp.bsp_device_status(est.plan)
+    print("error word after the short limit: %#x" % code)
+    assert code != 0
+    bsp.bsp_set_wait_limit(est.plan, 0)
+    after = est.compute(d).clone()
+    torch.cuda.synchronize()
+    assert bsp.bsp_device_status(est.plan) == 0
+    assert torch.equal(before, after)
+    with pytest.raises(bsp.BspError):
+        bsp.bsp_set_wait_limit(est.plan, -1)
+    est.close()

@@ -136,6 +136,39 @@ def test_fft_route_equals_brute_force_triangles(ora, n, edges):
             assert cnt == 0
 
 
+def test_legendre_leg_on_any_side_equals_brute_force(ora):
+    """The full-tensor reading of Sec. 3.1: with the bins (a; b >= c) for every
+    assignment of the Legendre leg (not only the largest side), the oracle's
+    FFT route equals the direct triangle sum with w_l on the shell a, to 1e-10
+    of the summand's norm; l = 0 is the same for every assignment of one
+    bin's shells, and l = 2 is not (the weighted leg matters)."""
+    n, edges = 12, [1, 2.5, 4, 5.5, 7]
+    dk, _ = make_field(FieldModel(n=n, box=BOX, sigma_g=0.3), 1711, dtype=np.complex128)
+    sorted_bins = [tuple(int(v) for v in t) for t in ora.bispectrum(dk, n, BOX, edges, ells=(0,))["bins"]]
+    full_bins = sorted({(t[k], max(t[(k + 1) % 3], t[(k + 2) % 3]), min(t[(k + 1) % 3], t[(k + 2) % 3]))
+                        for t in sorted_bins for k in range(3)})
+    assert any(a < b for (a, b, c) in full_bins)
+    r = ora.bispectrum(dk, n, BOX, edges, bins=full_bins)
+    full = ora.full_from_half(dk, n)
+    masks = ora.shell_masks(n, edges)
+    mu = ora.mu_grid(n)
+    for li, ell in enumerate((0, 2, 4)):
+        wl = ora.legendre_weight(ell, mu)
+        for bi, (a, b, c) in enumerate(full_bins):
+            s, _ = ora.brute_triangles(full, wl * masks[a], masks[b], masks[c])
+            scale = math.sqrt(r["sumsq"][li, bi]) / n ** 3
+            assert abs(s.real - r["T"][li, bi] / n ** 3) <= 1e-10 * scale
+    key = {t: i for i, t in enumerate(full_bins)}
+    moved = 0
+    for t in sorted_bins:
+        if len(set(t)) < 3:
+            continue
+        ia, ic = key[t], key[(t[2], t[0], t[1])]
+        assert abs(r["B"][0, ia] - r["B"][0, ic]) <= 1e-10 * abs(r["B"][0, ia])
+        moved += abs(r["B"][1, ia] - r["B"][1, ic]) > 1e-6 * abs(r["B"][1, ia])
+    assert moved > 0
+
+
 def test_thin_shell_counts(ora):
     """T3: N_abc -> 8 pi^2 k_a k_b k_c dk^3 / k_f^6 for thin, non-degenerate,
     unaliased shells (V_B of Sec. 3.1 in the continuum limit)."""
