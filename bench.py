@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="tensor-core FP32 accumulation chunk (points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision-compare", action="store_true",
+                    help="skip timing split-BF16 and plain BF16 beside the benchmarked path")
+    ap.add_argument("--no-modal", action="store_true", help="skip the 512^3 / 50-mode modal entry")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-mock uneven-grid batch entry")
+    ap.add_argument("--batch-mocks", type=int, default=512)
     return ap.parse_args()
 
 
@@ -357,15 +362,21 @@ def main():
         pass
     fft_ms, con_ms, red_ms = phase
     stats = bsp.bsp_plan_stats(est.plan)
+    # measured FP32 FMA throughput of this GPU (the CUDA-core path's peak)
+    try:
+        fp32_peak, fp32_peak_ms = bsp.bsp_fp32_fma_peak()
+    except Exception:
+        fp32_peak, fp32_peak_ms = None, None
     flop = 2.0 * n3 * outputs
     issued = 2.0 * n3 * stats["issued_macs_per_point"]
     if con_ms >= fft_ms and args.prec == "fp32":
         clk = 2070.0
-        peak = N_SM * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+        peak = fp32_peak or N_SM * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
         ach = flop / (con_ms / 1e3) / 1e12
         roof = {"kernel": "k_contract_cc (FP32 CUDA-core contraction)", "bound": "alu", "achieved": ach,
                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "peak_source": ("measured: bsp_fp32_fma_peak (FMA chains, all SMs, CUDA events)" if fp32_peak
+                                else "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"),
                 "algorithmic": "2 n^3 flop per (bin, l): %.3e flop per launch" % flop,
                 "issued_frac": (issued / (con_ms / 1e3) / 1e12) / peak}
     elif con_ms >= fft_ms:
@@ -442,8 +453,18 @@ def main():
         dev = torch.max(torch.abs(Bs - Bf) / torch.maximum(torch.abs(Bf), rms)).item()
         line["fp32_compare"] = {"ms_per_step": ms32, "contraction_ms": ph32[1], "filter_fft_ms": ph32[0],
                                 "speedup_step": ms32 / ms, "speedup_contraction": ph32[1] / con_ms,
-                                "max_rel_dev_vs_fp32": dev, "steps": k32}
+                                "max_rel_dev_vs_fp32": dev, "steps": k32,
+                                "fp32_contraction_tflops": flop / (ph32[1] / 1e3) / 1e12,
+                                "fp32_peak_tflops_measured": fp32_peak,
+                                "fp32_frac_of_measured_peak": (flop / (ph32[1] / 1e3) / 1e12 / fp32_peak
+                                                               if fp32_peak else None)}
+        gg = golden_gate(est.bins, Bf.cpu().numpy(), args.n, args.shells, args.width)
+        if gg:
+            line["fp32_compare"].update(gg)
+        if not args.no_precision_compare:
+            line["precision_compare"] = precision_compare(args, est, d, stream, Bf.clone(), ph32[1], edges)
         ref.close()
+        del ref
     # cuFFT as a timed comparison only (never on the path): a full, unpruned
     # C2R transform of one n^3 field beside this library's per-field filter +
     # pruned inverse FFT + 16-bit split
@@ -454,12 +475,207 @@ def main():
         line["cpu_baseline"] = {"value": outputs / step_s, "unit": "bins/s", "cores": info["cores"],
                                 "kind": "oracle", "sample": info["sample"], "measured_s": info["measured_s"],
                                 "value_is_extrapolated": True}
+    line["fp32_peak"] = {"tflops": fp32_peak, "ms": fp32_peak_ms,
+                         "how": "bsp_fp32_fma_peak: 1024 threads per SM, 8 FMA chains each, CUDA events"}
+    est.close()
+    del est, d
+    torch.cuda.empty_cache()
+    if not args.no_modal and world == 1:
+        try:
+            line["modal"] = modal_bench(args, stream)
+        except Exception as e:   # reported, not fatal: the headline line still prints
+            line["modal"] = {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+        torch.cuda.empty_cache()
+    if not args.no_batch and world == 1:
+        try:
+            line["batch"] = batch_bench(args, stream)
+        except Exception as e:
+            line["batch"] = {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    est.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_512_64shells.json")
+
+
+def golden_gate(bins, B, n, shells, width):
+    """Gate error |dB| / max(|B|, rms_l) of B [3][n_bins] on the bins of the
+    committed FP64-oracle sample (tests/golden), where it covers this
+    workload; rms_l is taken over all bins of B.  None if not applicable."""
+    try:
+        g = json.load(open(GOLDEN))
+    except Exception:
+        return None
+    from paper_1708_05303_gb300.synth import linear_edges
+
+    if g["n"] != n or g["seed"] != SEED or list(g["edges"]) != list(linear_edges(shells, width)):
+        return None
+    import numpy as np
+
+    V, n3 = BOX ** 3, float(n) ** 3
+    idx = {tuple(int(v) for v in t): i for i, t in enumerate(bins)}
+    rms = np.sqrt(np.mean(B ** 2, axis=1))
+    worst = 0.0
+    for j, t in enumerate(g["bins"]):
+        i = idx[tuple(t)]
+        for li in range(3):
+            Bo = g["T"][li][j] / (V * n3 * g["counts"][j])
+            worst = max(worst, abs(B[li, i] - Bo) / max(abs(Bo), rms[li]))
+    return {"gate_vs_oracle": worst, "oracle_bins": len(g["bins"])}
+
+
+def precision_compare(args, est, d, stream, B_fp32, con_fp32_ms, edges):
+    """split-BF16 and plain BF16 contractions on the same input, counts and
+    workspace as the benchmarked plan: contraction time, speedup over the
+    plain FP32 CUDA-core path, error against the FP64 oracle's sample, and
+    the largest departure from FP32 over every output."""
+    import torch
+    from paper_1708_05303_gb300 import bsp
+
+    out = {}
+    rms = torch.sqrt(torch.mean(B_fp32 * B_fp32, dim=1, keepdim=True))
+    for prec in ("split_f16", "split_bf16", "bf16"):
+        if prec == args.prec:
+            p, own = est, False
+        else:
+            p, own = bsp.Bispectrum(args.n, BOX, edges, (0, 2, 4), prec=prec, counts_from=est, ws=est.ws), True
+        p.compute(d)
+        torch.cuda.synchronize()
+        bsp.bsp_set_profiling(p.plan, True)
+        for _ in range(2):
+            p.compute(d)
+        torch.cuda.synchronize()
+        ph, nc, _ = bsp.bsp_phase_times(p.plan)
+        bsp.bsp_set_profiling(p.plan, False)
+        B = p.compute(d)
+        dev = torch.max(torch.abs(B - B_fp32) / torch.maximum(torch.abs(B_fp32), rms)).item()
+        ent = {"contraction_ms": ph[1] / max(nc, 1), "step_ms": sum(ph) / max(nc, 1),
+               "speedup_contraction_vs_fp32": con_fp32_ms / (ph[1] / max(nc, 1)) if con_fp32_ms else None,
+               "max_rel_dev_vs_fp32": dev, "gated": prec == "split_f16"}
+        gg = golden_gate(p.bins, B.cpu().numpy(), args.n, args.shells, args.width)
+        if gg:
+            ent.update(gg)
+        out[prec] = ent
+        if own:
+            p.close()
+    return out
+
+
+def modal_bench(args, stream, reps=2):
+    """The modal estimator's workload (Sec. 3.5): 512^3, 50 shifted-Legendre
+    modes on [k_f, 0.3 h/Mpc] over sqrt(k P(k)), l = 0, 2, 4, 22 100 raw
+    projections per l, on the benchmarked precision."""
+    import torch
+    from paper_1708_05303_gb300 import bsp
+    from paper_1708_05303_gb300.synth import FieldModel, make_field
+
+    n, nm, kmax = args.n, 50, 0.3
+    kf = 2 * math.pi / BOX
+    model = FieldModel(n=n, box=BOX, sigma_g=0.3)
+    dk, amp = make_field(model, 1708 + 3)
+    R = bsp.bsp_modal_radial_powerlaw(n, BOX, nm, kf, kmax, amp, model.n_s, True)
+    d = torch.from_numpy(dk).cuda()
+    m = bsp.Modal(n, BOX, R, (0, 2, 4), prec=args.prec)
+    m.compute(d)
+    torch.cuda.synchronize()
+    bsp.bsp_set_profiling(m.plan, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        m.compute(d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ph, nc, nl = bsp.bsp_phase_times(m.plan)
+    bsp.bsp_set_profiling(m.plan, False)
+    ph = [v / max(nc, 1) for v in ph]
+    st = bsp.bsp_plan_stats(m.plan) if hasattr(bsp, "bsp_plan_stats") else {}
+    status = bsp.bsp_device_status(m.plan)
+    m.close()
+    ntrip = nm * (nm + 1) * (nm + 2) // 6
+    # sums the plan computes: T^l(a; b >= c) for every a and l, and U(a; b >= c) for l = 4
+    sums = 3 * nm * nm * (nm + 1) // 2 + nm * nm * (nm + 1) // 2
+    flop = 2.0 * float(n) ** 3 * sums
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops_sustained", 1700.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1700.0
+    ach = flop / (ph[1] / 1e3) / 1e12
+    return {"ms": ms, "phases_ms": {"filter_fft": ph[0], "contraction": ph[1], "assemble": ph[2]},
+            "modes_1d": nm, "triplets_per_l": ntrip, "projections_per_s": 3 * ntrip / (ms / 1e3),
+            "fields": 3 * nm, "contraction_sums": sums, "device_status": status,
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "algorithmic": "2 n^3 flop per sum, T^l(a; b >= c) for all a and l plus U: %.3e flop"
+                                        % flop}}
+
+
+def _mock_input(m):
+    """Half spectrum of mock m of the uneven-grid ensemble (inputs only)."""
+    from paper_1708_05303_gb300.synth import make_field, mock_model
+
+    model, seed = mock_model(m, BATCH_SIZES)
+    dk, _ = make_field(model, seed)
+    return BATCH_SIZES.index(model.n), dk
+
+
+BATCH_SIZES = (96, 128, 160)
+
+
+def batch_bench(args, stream):
+    """512 mocks of 96^3, 128^3 and 160^3 grids (own n_s, f per mock), 24
+    shells of width k_f, l = 0, 2, 4 (a 4962-vector per mock) through the
+    batch runner: CUDA graphs per size, autotuned schedule, H2D copies of the
+    next mock overlapped with the current one; then the FP64 covariance."""
+    import multiprocessing as mp
+
+    import torch
+    from paper_1708_05303_gb300 import bsp
+    from paper_1708_05303_gb300.synth import linear_edges
+
+    edges = linear_edges(24, 1.0)
+    nm = args.batch_mocks
+    t0 = time.perf_counter()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 4)) as pool:
+        inputs = pool.map(_mock_input, range(nm), chunksize=4)
+    t_gen = time.perf_counter() - t0
+    counts_s = {}
+    for n in BATCH_SIZES:
+        t0 = time.perf_counter()
+        e = bsp.Bispectrum(n, BOX, edges, (0, 2, 4), prec=args.prec)
+        torch.cuda.synchronize()
+        counts_s[str(n)] = round(time.perf_counter() - t0, 3)
+        e.close()
+        del e
+    t0 = time.perf_counter()
+    batch = bsp.Batch(BATCH_SIZES, BOX, edges, (0, 2, 4), prec=args.prec, autotune=True)
+    t_prep = time.perf_counter() - t0
+    hosts = [torch.from_numpy(dk).pin_memory() for _, dk in inputs]
+    idx = [si for si, _ in inputs]
+    rows = batch.run(hosts[:6], idx[:6])
+    torch.cuda.synchronize()
+    rows = torch.empty((nm, 3 * batch.nbins), dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.run(hosts, idx, rows=rows)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    mean, cov = batch.covariance(rows)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    cov_ms = c0.elapsed_time(c1)
+    finite = bool(torch.isfinite(cov).all().item())
+    out = {"mocks": nm, "sizes": list(BATCH_SIZES), "shells": 24, "bins": batch.nbins, "vector": 3 * batch.nbins,
+           "ms": ms, "mocks_per_s": nm / (ms / 1e3), "per_size_graph_ms": batch.tuning["ms"],
+           "tuning": batch.tuning, "counts_s": counts_s, "prepare_s": round(t_prep, 3),
+           "covariance_ms": cov_ms, "covariance_finite": finite, "input_generation_s": round(t_gen, 1),
+           "precision": args.prec}
+    batch.close()
+    return out
 
 
 def cufft_compare(delta_k, n, ours_ms_per_field, stream=None, reps=10):

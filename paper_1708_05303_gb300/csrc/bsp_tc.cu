@@ -75,6 +75,7 @@ struct TcSmem {
     int2 pf[TC_M];
     float pscale[TC_M];
     float fscale[TC_NMAX];
+    int fexp[TC_NMAX];        // -log2 of fscale (the flush scales by 2^(fexp + pexp))
     TcWork w;
 };
 
@@ -235,6 +236,20 @@ __device__ __forceinline__ void unpack64(uint64_t v, float& x0, float& x1) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(x0), "=f"(x1) : "l"(v));
 }
 
+// f * 2^k as a double, built from the float's bits with integer operations
+// (k is small: |k| < 300).  The FP64 pipe of this GPU is slow; the flushes
+// used to divide by the scale in FP64, which cost more than the MMAs.
+// Zero, denormal, infinite and NaN inputs take the exact library path.
+__device__ __forceinline__ double f32_ldexp_f64(float f, int k) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return ldexp((double)f, k);
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                                 ((unsigned long long)(e + 896u + (uint32_t)k) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 // Wait until *ctr >= target (acquire); false after ~4 s.
 __device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target, long long limit) {
     const long long t0 = clock64();
@@ -325,6 +340,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float fs = 1.f;
         if (c < 8 * w.nbox) fs = pow2_scale(bound_mul * __uint_as_float(fmax2[w.box_field[c >> 3] + (c & 7)]));
         S.fscale[c] = fs;
+        S.fexp[c] = -ilogbf(fs);
     }
     if (warp == W_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -493,7 +509,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // the CTA's FP64 slot, [column][pair] (zeroed before the launch): the flushes are
         // fire-and-forget reductions, coalesced over the warp's 32 pairs
         double* dst = partial + (size_t)blockIdx.x * TC_SLOT + row;
-        const double rs = 1.0 / (double)S.pscale[row];   // exact: powers of two
+        const int pexp = -ilogbf(S.pscale[row]);   // the scales are powers of two
         for (int c = 0; c < nch && !S.abort; ++c) {
             const int j = c & 1, g = c % FL;
             const bool flush = g == FL - 1 || c == nch - 1;
@@ -535,7 +551,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (flush) {
 #pragma unroll
                     for (int t = 0; t < 16; ++t) {
-                        const double v = (double)__uint_as_float(a[t]) * rs / (double)S.fscale[col + t];
+                        const double v = f32_ldexp_f64(__uint_as_float(a[t]), pexp + S.fexp[col + t]);
                         asm volatile("red.global.add.f64 [%0], %1;" ::"l"(dst + (size_t)(col + t) * TC_M), "d"(v)
                                      : "memory");
                     }

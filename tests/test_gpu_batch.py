@@ -50,7 +50,7 @@ def test_batch_rows_and_covariance(torch_cuda, ora, prec):
     mean, cov = batch.covariance(rows)
     torch.cuda.synchronize()
     rows_h = rows.cpu().numpy()
-    tol = 1e-5 if prec == "fp32" else 2e-5
+    tol = 1e-5
     ora_rows = []
     for (si, dk), row in zip(ms, rows_h):
         r = ora.bispectrum(dk.astype(np.complex128), sizes[si], BOX, edges)

@@ -51,6 +51,8 @@ def _check(torch, ora, n, nsh, width, m, seed, gate=1e-5):
     rms = np.sqrt(np.mean(r["iB"][:, live] ** 2, axis=1, keepdims=True))
     e_rms = float(np.max(np.abs(g1 - r["iB"])[:, live] / np.maximum(np.abs(r["iB"][:, live]), rms)))
     print("iB %d^3, %d shells, m=%d: %.3g of the term scale, %.3g of max(|iB|, rms)" % (n, nsh, m, e, e_rms))
+    # the gate of every other multipole in this library: max(|iB|, rms_l)
+    assert e_rms <= gate
     assert e <= gate
     return g1, r
 

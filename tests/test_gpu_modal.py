@@ -33,8 +33,6 @@ def test_modal_matches_oracle(torch_cuda, ora, prec, ells):
     dk, amp = make_field(FieldModel(n=n, box=BOX, sigma_g=0.3), 31)
     R = bsp.bsp_modal_radial_powerlaw(n, BOX, nmodes, kf, 14 * kf, amp, -1.5, True)
     est = bsp.Modal(n, BOX, R, ells, prec=prec)
-    if prec != "fp32":
-        bsp.bsp_set_accumulation_chunk(est.plan, 64)
     S = est.compute(torch.from_numpy(dk).cuda()).cpu().numpy()
     torch.cuda.synchronize()
     if prec != "fp32":
