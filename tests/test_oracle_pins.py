@@ -732,3 +732,37 @@ def test_ib_single_cube_vanishes(ora):
     r = ora.integrated_bispectrum(dk, 16, 300.0, [1.0, 3.0, 5.0, 7.0], 1)
     assert abs(r["dbar"][0]) < 1e-12
     assert np.max(np.abs(r["iB"])) < 1e-12 * max(1.0, np.max(np.abs(ora.power_multipoles(dk, 16, 300.0, [1.0, 3.0, 5.0, 7.0])["P"])))
+
+
+def test_golden_512_counts_by_direct_enumeration():
+    """The committed 512^3 oracle sample (tests/golden): its counts of the
+    low-k bins equal a direct enumeration of the triangles q1 + q2 + q3 = 0
+    with the legs in shells a, b, c (the shells are far below n/2, so no
+    triangle wraps), so the file is tied to the definition, not only to the
+    oracle run that wrote it."""
+    import itertools
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                    "fullsize_512_64shells.json")))
+    e = g["edges"]
+
+    def modes(s):
+        r = int(math.ceil(e[s + 1]))
+        return [q for q in itertools.product(range(-r, r + 1), repeat=3)
+                if e[s] ** 2 <= q[0] ** 2 + q[1] ** 2 + q[2] ** 2 < e[s + 1] ** 2]
+
+    checked = 0
+    for (a, b, c), cnt in zip(g["bins"], g["counts"]):
+        if a > 2:
+            continue
+        mb, mc = modes(b), set(modes(c))
+        n = 0
+        for q1 in modes(a):
+            for q2 in mb:
+                if (-q1[0] - q2[0], -q1[1] - q2[1], -q1[2] - q2[2]) in mc:
+                    n += 1
+        assert n == cnt, ((a, b, c), n, cnt)
+        checked += 1
+    assert checked >= 8
