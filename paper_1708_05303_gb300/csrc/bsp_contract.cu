@@ -169,6 +169,165 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
                 (double)acc[i][j] + (double)hi[i][j] + (double)lo[i][j];
 }
 
+
+// FP32 contraction with the operands staged by asynchronous copies (cp.async,
+// two stages in flight): rows A_r and pair factors X_s (and Y_s) for 32
+// points land in shared memory in their natural [field][x] layout while the
+// previous 32 points are multiplied.  Thread (ty, tx) owns rows ty + 16 i and
+// pairs 4 tx + j (i, j < 4): per 4 points it reads 4 float4 of A (8 distinct
+// rows per warp: conflict-free with the 36-float row stride) and 4 float4 of
+// the pair products P[x][p], then does 64 FMAs.  Block sums of 64 points are
+// folded into compensated (TwoSum) pairs, as in k_contract_cc.
+constexpr int C2_XS = 32;                 // points per stage
+constexpr int C2_LD = C2_XS + 4;          // row stride (floats) of the staged fields
+constexpr int C2_PS = CC_COLS + 4;        // row stride of the pair products
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+struct Cc2Smem {
+    float A[2][CC_ROWS][C2_LD];
+    float X[2][64][C2_LD];
+    float Y[2][64][C2_LD];
+    float P[C2_XS][C2_PS];
+    int2 pf[CC_COLS];
+    int rf[CC_ROWS];
+};
+
+template <bool TWO, bool SYM>
+__global__ void __launch_bounds__(CC_THREADS, 2) k_contract_cc32(const float* __restrict__ rows,
+                                                                 const float* __restrict__ px,
+                                                                 const float* __restrict__ py, size_t fstride,
+                                                                 const Work* __restrict__ works,
+                                                                 const int2* __restrict__ pair_fields,
+                                                                 const int* __restrict__ row_fields, size_t npts,
+                                                                 size_t seg, double* __restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char c2_raw[];
+    Cc2Smem& S = *reinterpret_cast<Cc2Smem*>(c2_raw);
+    const Work w = works[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ty = (warp & 1) * 8 + (lane >> 2);     // rows ty + 16 i
+    const int tx = (warp >> 1) * 4 + (lane & 3);     // pairs 4 tx + j
+    for (int i = tid; i < CC_COLS; i += CC_THREADS) {
+        int2 v = {-1, -1};
+        if (i < w.npairs) {
+            v = pair_fields[w.pair0 + i];
+            v.x -= w.shell_lo;
+            v.y -= w.shell_lo;
+        }
+        S.pf[i] = v;
+    }
+    for (int i = tid; i < CC_ROWS; i += CC_THREADS) S.rf[i] = i < w.nrows ? row_fields[w.rowbase + i] : -1;
+    __syncthreads();
+    const size_t x_begin = (size_t)blockIdx.y * seg;
+    const size_t x_end = min(npts, x_begin + seg);
+    const int nst = x_end > x_begin ? (int)((x_end - x_begin + C2_XS - 1) / C2_XS) : 0;
+    const int nsh = w.nshell;
+
+    // stage s -> buffer b: 8 chunks of 4 floats per field row, zero-filled past x_end
+    auto load = [&](int st, int b) {
+        const size_t x0 = x_begin + (size_t)st * C2_XS;
+        const int nrow_all = CC_ROWS + nsh * (TWO ? 2 : 1);
+        for (int e = tid; e < nrow_all * 8; e += CC_THREADS) {
+            const int r = e >> 3, ch = e & 7;
+            const size_t x = x0 + 4 * ch;
+            const int rem = x < x_end ? (int)min((size_t)4, x_end - x) : 0;
+            const float* src;
+            float* dst;
+            int bytes = rem * 4;
+            if (r < CC_ROWS) {
+                const int f = S.rf[r];
+                if (f < 0) bytes = 0;
+                src = rows + (size_t)max(f, 0) * fstride + (bytes ? x : 0);
+                dst = &S.A[b][r][4 * ch];
+            } else if (r < CC_ROWS + nsh) {
+                const int sh = r - CC_ROWS;
+                src = px + (size_t)(w.shell_lo + sh) * fstride + (bytes ? x : 0);
+                dst = &S.X[b][sh][4 * ch];
+            } else {
+                const int sh = r - CC_ROWS - nsh;
+                src = py + (size_t)(w.shell_lo + sh) * fstride + (bytes ? x : 0);
+                dst = &S.Y[b][sh][4 * ch];
+            }
+            cp_async16(dst, src, bytes);
+        }
+    };
+
+    float acc[4][4], hi[4][4], lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = hi[i][j] = lo[i][j] = 0.f;
+    if (nst > 0) load(0, 0);
+    cp_async_commit();
+    for (int st = 0; st < nst; ++st) {
+        const int b = st & 1;
+        if (st + 1 < nst) load(st + 1, b ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        // pair products of this stage, P[x][p]
+        for (int e = tid; e < CC_COLS * C2_XS; e += CC_THREADS) {
+            const int p = e % CC_COLS, x = e / CC_COLS;
+            const int2 bc = S.pf[p];
+            float v = 0.f;
+            if (bc.x >= 0) {
+                if (!TWO) v = S.X[b][bc.x][x] * S.X[b][bc.y][x];
+                else if (!SYM) v = S.X[b][bc.x][x] * S.Y[b][bc.y][x];
+                else v = S.X[b][bc.x][x] * S.Y[b][bc.y][x] + S.Y[b][bc.x][x] * S.X[b][bc.y][x];
+            }
+            S.P[x][p] = v;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int x = 0; x < C2_XS; x += 4) {
+            float4 a[4], q[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(&S.A[b][ty + 16 * i][x]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = *reinterpret_cast<const float4*>(&S.P[x + j][4 * tx]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    acc[i][0] = fmaf(av[u], (&q[u].x)[0], acc[i][0]);
+                    acc[i][1] = fmaf(av[u], (&q[u].x)[1], acc[i][1]);
+                    acc[i][2] = fmaf(av[u], (&q[u].x)[2], acc[i][2]);
+                    acc[i][3] = fmaf(av[u], (&q[u].x)[3], acc[i][3]);
+                }
+            }
+        }
+        if (st & 1) {   // every 64 points: fold the block sums into the compensated pairs
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float s2, e2;
+                    two_sum(hi[i][j], acc[i][j], s2, e2);
+                    hi[i][j] = s2;
+                    lo[i][j] += e2;
+                    acc[i][j] = 0.f;
+                }
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+    double* slot = partial + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * CC_OUT;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            slot[(size_t)(ty + 16 * i) * CC_COLS + 4 * tx + j] =
+                (double)acc[i][j] + (double)hi[i][j] + (double)lo[i][j];
+}
+
 __global__ void k_reduce(const double* __restrict__ partial, int nsplit, size_t unit, int row_stride,
                          const BinLoc* __restrict__ loc, int nout, int nbins, const double* __restrict__ counts,
                          double scale, int mode, double* __restrict__ T_out, double* __restrict__ out,
@@ -232,12 +391,33 @@ cudaError_t launch_contract_cc(const R* rows, const R* px, const R* py, int sym,
                                int nwork, const int2* pair_fields, const int* row_fields, size_t npts, int nsplit,
                                double* partial, cudaStream_t st) {
     constexpr int XC = CCCfg<R>::XC;
-    size_t seg = (npts + nsplit - 1) / nsplit;
-    seg = (seg + XC - 1) / XC * XC;
-    dim3 grid(nwork, nsplit);
-    k_contract_cc<R><<<grid, CC_THREADS, 0, st>>>(rows, px, py ? py : px, sym, fstride, works, pair_fields,
-                                                  row_fields, npts, seg, partial);
-    return cudaGetLastError();
+    if constexpr (sizeof(R) == 4) {
+        // FP32: the pipelined kernel (segments in whole stages of C2_XS points)
+        size_t seg = (npts + nsplit - 1) / nsplit;
+        seg = (seg + 2 * C2_XS - 1) / (2 * C2_XS) * (2 * C2_XS);
+        const bool two = py != nullptr && py != px;
+        const size_t smem = sizeof(Cc2Smem);
+        static bool attr[3] = {false, false, false};
+        auto kern = !two ? k_contract_cc32<false, false> : sym ? k_contract_cc32<true, true>
+                                                                : k_contract_cc32<true, false>;
+        const int ki = !two ? 0 : sym ? 2 : 1;
+        if (!attr[ki]) {   // once per variant, never inside a graph capture
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr[ki] = true;
+        }
+        dim3 grid(nwork, nsplit);
+        kern<<<grid, CC_THREADS, smem, st>>>(rows, px, two ? py : px, fstride, works, pair_fields, row_fields, npts,
+                                             seg, partial);
+        return cudaGetLastError();
+    } else {
+        size_t seg = (npts + nsplit - 1) / nsplit;
+        seg = (seg + XC - 1) / XC * XC;
+        dim3 grid(nwork, nsplit);
+        k_contract_cc<R><<<grid, CC_THREADS, 0, st>>>(rows, px, py ? py : px, sym, fstride, works, pair_fields,
+                                                      row_fields, npts, seg, partial);
+        return cudaGetLastError();
+    }
 }
 
 template cudaError_t launch_contract_cc<float>(const float*, const float*, const float*, int, size_t, const Work*,
