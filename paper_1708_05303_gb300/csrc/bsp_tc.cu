@@ -52,12 +52,13 @@ constexpr int TC_THREADS = 32 * (W_EPI0 + 4);
 static_assert(N_PRO == 8 || N_PRO == 16, "pair-product warps: 8 or 16");
 // tensor memory columns: the P_hi F_hi accumulators D0 [0,96) and D1 [96,192),
 // drained every chunk; the correction accumulator E = P_hi F_lo + P_lo F_hi
-// [192,288), drained every CORR_KB K-blocks; the running sum [288,384); the A
+// [192,288), drained every CORR_KB K-blocks (its terms are ~2^-11 of D's, so
+// its own truncation stays far below D's); the running sum [288,384); the A
 // buffers [384,448) and [448,512), hi in the first 32 columns, lo in the next 32.
 // E's terms are ~2^-11 of D's: kept apart, the tensor core's truncating FP32
 // accumulation no longer loses half an ulp of D on each correction product.
 constexpr uint32_t TMEM_COLS = 512, COL_ACC = 96, COL_CORR = 192, COL_SUM = 288, COL_A = 384;
-constexpr int CORR_KB = 16;      // K-blocks per drain of E (a multiple of the chunk)
+constexpr int CORR_KB = 64;      // K-blocks per drain of E (a multiple of the chunk)
 constexpr int FLUSH_KB = 128;    // K-blocks between FP64 flushes of the running sum
 constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
 
@@ -104,6 +105,10 @@ __device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
         : "memory");
     return done != 0;
 }
+// Waits poll with a suspend-time hint: the waiting thread sleeps in the
+// barrier until the phase completes (or ~2 us pass) instead of re-reading
+// shared memory in a tight loop, which took shared-memory bandwidth from the
+// copies, the pair products and the MMAs.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit = WAIT_CYCLES) {
     const uint32_t addr = smem_u32(b);
     if (mbar_test(addr, parity)) return true;
@@ -111,10 +116,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long lon
     while (true) {
         uint32_t done;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
             " selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(addr), "r"(parity)
+            : "r"(addr), "r"(parity), "r"(2000u)
             : "memory");
         if (done) return true;
         if (clock64() - t0 > limit) return false;
@@ -539,6 +544,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) mbar_arrive(&S.corr_empty);
                 have_sum = true;
             }
+            // D joins the running sum; the accumulator is released at once
             for (uint32_t col = 0; col < N; col += 16) {
                 uint32_t a[16], m[16];
                 tmem_ld16(lanebase + (uint32_t)j * COL_ACC + col, a);
@@ -548,21 +554,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int t = 0; t < 16; ++t) a[t] = __float_as_uint(__uint_as_float(m[t]) + __uint_as_float(a[t]));
                 }
-                if (flush) {
+                tmem_st16(lanebase + COL_SUM + col, a);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.acc_empty[j]);
+            if (flush) {
+                // the running sum to the CTA's FP64 slot, while the MMAs fill the other D buffer
+                for (uint32_t col = 0; col < N; col += 16) {
+                    uint32_t a[16];
+                    tmem_ld16(lanebase + COL_SUM + col, a);
+                    tmem_ld_wait();
 #pragma unroll
                     for (int t = 0; t < 16; ++t) {
                         const double v = f32_ldexp_f64(__uint_as_float(a[t]), pexp + S.fexp[col + t]);
                         asm volatile("red.global.add.f64 [%0], %1;" ::"l"(dst + (size_t)(col + t) * TC_M), "d"(v)
                                      : "memory");
                     }
-                } else {
-                    tmem_st16(lanebase + COL_SUM + col, a);
                 }
+                tc_fence_before();
             }
-            if (!flush) tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.acc_empty[j]);
         }
     }
     tc_fence_before();
