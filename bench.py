@@ -626,7 +626,9 @@ def batch_bench(args, stream):
     """512 mocks of 96^3, 128^3 and 160^3 grids (own n_s, f per mock), 24
     shells of width k_f, l = 0, 2, 4 (a 4962-vector per mock) through the
     batch runner: CUDA graphs per size, autotuned schedule, H2D copies of the
-    next mock overlapped with the current one; then the FP64 covariance."""
+    next mock overlapped with the current one; then the FP64 covariance.
+    Timed on the FP32 path (the one that meets 1e-5 on these fields) and on
+    the split-FP16 tensor-core path beside it."""
     import multiprocessing as mp
 
     import torch
@@ -643,38 +645,44 @@ def batch_bench(args, stream):
     counts_s = {}
     for n in BATCH_SIZES:
         t0 = time.perf_counter()
-        e = bsp.Bispectrum(n, BOX, edges, (0, 2, 4), prec=args.prec)
+        e = bsp.Bispectrum(n, BOX, edges, (0, 2, 4), prec="fp32")
         torch.cuda.synchronize()
         counts_s[str(n)] = round(time.perf_counter() - t0, 3)
         e.close()
         del e
-    t0 = time.perf_counter()
-    batch = bsp.Batch(BATCH_SIZES, BOX, edges, (0, 2, 4), prec=args.prec, autotune=True)
-    t_prep = time.perf_counter() - t0
     hosts = [torch.from_numpy(dk).pin_memory() for _, dk in inputs]
     idx = [si for si, _ in inputs]
-    rows = batch.run(hosts[:6], idx[:6])
-    torch.cuda.synchronize()
-    rows = torch.empty((nm, 3 * batch.nbins), dtype=torch.float64, device="cuda")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    batch.run(hosts, idx, rows=rows)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    mean, cov = batch.covariance(rows)
-    c1.record(stream)
-    torch.cuda.synchronize()
-    cov_ms = c0.elapsed_time(c1)
-    finite = bool(torch.isfinite(cov).all().item())
-    out = {"mocks": nm, "sizes": list(BATCH_SIZES), "shells": 24, "bins": batch.nbins, "vector": 3 * batch.nbins,
-           "ms": ms, "mocks_per_s": nm / (ms / 1e3), "per_size_graph_ms": batch.tuning["ms"],
-           "tuning": batch.tuning, "counts_s": counts_s, "prepare_s": round(t_prep, 3),
-           "covariance_ms": cov_ms, "covariance_finite": finite, "input_generation_s": round(t_gen, 1),
-           "precision": args.prec}
-    batch.close()
+    out = {"mocks": nm, "sizes": list(BATCH_SIZES), "shells": 24, "counts_s": counts_s,
+           "input_generation_s": round(t_gen, 1)}
+    for prec in ("fp32", "split_f16"):
+        t0 = time.perf_counter()
+        batch = bsp.Batch(BATCH_SIZES, BOX, edges, (0, 2, 4), prec=prec, autotune=True)
+        t_prep = time.perf_counter() - t0
+        batch.run(hosts[:6], idx[:6])
+        torch.cuda.synchronize()
+        rows = torch.empty((nm, 3 * batch.nbins), dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run(hosts, idx, rows=rows)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        mean, cov = batch.covariance(rows)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        ent = {"ms": ms, "mocks_per_s": nm / (ms / 1e3), "per_size_graph_ms": batch.tuning["ms"],
+               "tuning": batch.tuning, "prepare_s": round(t_prep, 3), "covariance_ms": c0.elapsed_time(c1),
+               "covariance_finite": bool(torch.isfinite(cov).all().item())}
+        out["bins"], out["vector"] = batch.nbins, 3 * batch.nbins
+        if prec == "fp32":
+            out.update(ent)
+            out["precision"] = "fp32"
+        else:
+            out["split_f16"] = ent
+        batch.close()
+        del rows, mean, cov
     return out
 
 
