@@ -207,10 +207,15 @@ struct TcSched {
     int lsup = 1, nsup = 1;
 };
 
-// Persistent units: each work gets CTAs in proportion to its cost (its MMA N
-// plus a constant for the pair-product prologue), all CTAs together about
-// one per SM; every super-segment of lsup K-blocks is split among the work's
-// CTAs, so all works sweep x at the same pace and share the fields in L2.
+// Persistent units: each work gets CTAs in proportion to its cost per
+// K-block, all CTAs together about one per SM; every super-segment of lsup
+// K-blocks is split among the work's CTAs, so all works sweep x at the same
+// pace and share the fields in L2.  The cost of a K-block is set by the
+// pair-product prologue of the tile's 128 pairs and hardly depends on the
+// MMA N (clock traces on GB300: ~1 800 busy cycles per K-block for N = 32
+// and N = 96 alike), so the weight is almost flat in N; weighting by N, as
+// the first versions did, gave works of small N 1.9x the K-blocks per CTA
+// and left the other CTAs waiting at the pacing counter.
 void assign_units(TcSched& h, size_t npts, int nsm) {
     const int nw = (int)h.works.size();
     const long long nkb = (long long)((npts + 63) / 64);
@@ -218,11 +223,11 @@ void assign_units(TcSched& h, size_t npts, int nsm) {
     std::vector<int> c(nw, 1);
     if (nw < nsm) {
         double wsum = 0;
-        for (auto& w : h.works) wsum += w.n + 48.0;
+        for (auto& w : h.works) wsum += w.n + 3000.0;
         int used = 0;
         std::vector<std::pair<double, int>> frac;
         for (int i = 0; i < nw; ++i) {
-            const double want = nsm * (h.works[i].n + 48.0) / wsum;
+            const double want = nsm * (h.works[i].n + 3000.0) / wsum;
             c[i] = std::max(1, (int)want);
             used += c[i];
             frac.push_back({want - (int)want, i});
