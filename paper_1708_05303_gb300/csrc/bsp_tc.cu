@@ -471,7 +471,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const bool live = pair && (long long)(k / unit.len) * lsup + unit.start + k % unit.len < nkb_real;
             const uint8_t* f0 = S.f0[s];
             uint32_t vh[2 * PRO_CH], vl[2 * PRO_CH];
-            const uint64_t kSplit = pack64(F16 ? 8193.f : 65537.f, F16 ? 8193.f : 65537.f);   // 2^13 + 1, 2^16 + 1
 #pragma unroll
             for (int jj = 0; jj < PRO_CH; ++jj) {
                 const int j = j0 + jj;
@@ -482,19 +481,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     p01 = fmul2(pack64(fb.x, fb.y), pack64(fc.x, fc.y));
                     p23 = fmul2(pack64(fb.z, fb.w), pack64(fc.z, fc.w));
                 }
-                // Veltkamp split in FP32 (t = C p, hi = t - (t - p), lo = p - hi): hi keeps
-                // 11 (FP16) or 8 (BF16) significant bits, so its 16-bit conversion is
-                // exact and lo needs no conversion back from 16 bits -- half the
-                // conversion instructions of rounding hi and unpacking it
-                const uint64_t t01 = fmul2(p01, kSplit), t23 = fmul2(p23, kSplit);
-                const uint64_t h01 = fsub2(t01, fsub2(t01, p01)), h23 = fsub2(t23, fsub2(t23, p23));
-                float h0, h1, h2, h3, r0, r1, r2, r3;
-                unpack64(h01, h0, h1);
-                unpack64(h23, h2, h3);
-                unpack64(fsub2(p01, h01), r0, r1);
-                unpack64(fsub2(p23, h23), r2, r3);
-                vh[2 * jj] = pack2<F16>(h0, h1);
-                vh[2 * jj + 1] = pack2<F16>(h2, h3);
+                float p0, p1, p2, p3, h0, h1, h2, h3;
+                unpack64(p01, p0, p1);
+                unpack64(p23, p2, p3);
+                vh[2 * jj] = pack2<F16>(p0, p1);
+                vh[2 * jj + 1] = pack2<F16>(p2, p3);
+                unpack2<F16>(vh[2 * jj], h0, h1);
+                unpack2<F16>(vh[2 * jj + 1], h2, h3);
+                float r0, r1, r2, r3;
+                unpack64(fsub2(p01, pack64(h0, h1)), r0, r1);
+                unpack64(fsub2(p23, pack64(h2, h3)), r2, r3);
                 vl[2 * jj] = pack2<F16>(r0, r1);
                 vl[2 * jj + 1] = pack2<F16>(r2, r3);
             }
