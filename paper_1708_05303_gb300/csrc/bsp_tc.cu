@@ -53,11 +53,17 @@ static_assert(N_PRO == 8 || N_PRO == 16, "pair-product warps: 8 or 16");
 // tensor memory columns: the P_hi F_hi accumulators D0 [0,96) and D1 [96,192),
 // drained every chunk; the correction accumulator E = P_hi F_lo + P_lo F_hi
 // [192,288), drained every CORR_KB K-blocks (its terms are ~2^-11 of D's, so
-// its own truncation stays far below D's); the running sum [288,384); the A
-// buffers [384,448) and [448,512), hi in the first 32 columns, lo in the next 32.
+// its own truncation stays far below D's); three A buffers [288,352),
+// [352,416), [416,480), hi in the first 32 columns, lo in the next 32.  The
+// running FP32 sum of the drained accumulators lives in shared memory, which
+// frees the tensor memory for the third A buffer: with two, the products of
+// K-block k + 2 waited for the MMAs of K-block k to complete, and that chain,
+// not any one unit, set the pace (clock traces: ~2 050 cycles per K-block
+// with the tensor pipe ~20 % busy).
 // E's terms are ~2^-11 of D's: kept apart, the tensor core's truncating FP32
 // accumulation no longer loses half an ulp of D on each correction product.
-constexpr uint32_t TMEM_COLS = 512, COL_ACC = 96, COL_CORR = 192, COL_SUM = 288, COL_A = 384;
+constexpr uint32_t TMEM_COLS = 512, COL_ACC = 96, COL_CORR = 192, COL_A = 288;
+constexpr int NA = 3;            // A buffers (pair products) in tensor memory
 constexpr int CORR_KB = 64;      // K-blocks per drain of E (a multiple of the chunk)
 constexpr int FLUSH_KB = 128;    // K-blocks between FP64 flushes of the running sum
 constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
@@ -65,10 +71,11 @@ constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
 struct TcSmem {
     uint8_t f0[NT][TC_MAXSH * 256];        // [stage][row][64 floats], each half 128-byte swizzled
     uint8_t b[NT][TC_NMAX / 8 * 2048];     // [stage][group of 8 fields][hi 1024 B | lo 1024 B]
+    float sum[TC_NMAX][TC_M];              // running FP32 sum, [column][pair]
     // tma_full: a stage's copies landed; kb_done: the MMAs of K-block k finished
-    // (frees TMA stage k % NT and A buffer k % 2); a_full: A buffer written
+    // (frees TMA stage k % NT and A buffer k % NA); a_full: A buffer written
     // corr_empty: E was read
-    uint64_t tma_full[NT], kb_done[NT], a_full[2], acc_full[2], acc_empty[2], corr_empty;
+    uint64_t tma_full[NT], kb_done[NT], a_full[NA], acc_full[2], acc_empty[2], corr_empty;
     uint32_t tmem_base;
     volatile int abort;
     int npc;                  // plane copies per K-block
@@ -302,8 +309,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&S.tma_full[s], 1);
             mbar_init(&S.kb_done[s], 1);
         }
+        for (int j = 0; j < NA; ++j) mbar_init(&S.a_full[j], N_PRO);
         for (int j = 0; j < 2; ++j) {
-            mbar_init(&S.a_full[j], N_PRO);
             mbar_init(&S.acc_full[j], 1);
             mbar_init(&S.acc_empty[j], 4);
         }
@@ -407,7 +414,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t b0 = smem_u32(S.b[0]);
             int done = 0, kc = 0, c = 0;   // kc = k % CHUNK, c = k / CHUNK
             for (int k = 0; k < nkb; ++k) {
-                const int s = k % NT, u = k / NT, sa = k & 1;
+                const int s = k % NT, u = k / NT, sa = k % NA;
                 const int j = c & 1;
                 const bool efirst = kc == 0 && c % CC == 0;   // first K-block of a drain period of E
                 if (kc == 0 && c >= 2 && !mbar_wait(&S.acc_empty[j], ((c >> 1) - 1) & 1, wlim)) {
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     set_abort(S, err, 2);
                     break;
                 }
-                if (!mbar_wait(&S.tma_full[s], u & 1, wlim) || !mbar_wait(&S.a_full[sa], (k >> 1) & 1, wlim)) {
+                if (!mbar_wait(&S.tma_full[s], u & 1, wlim) || !mbar_wait(&S.a_full[sa], (k / NA) & 1, wlim)) {
                     set_abort(S, err, 4);
                     break;
                 }
@@ -461,9 +468,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int ob = rb * 256 + 128 * h, sb = (g0 + rb) & 7, oc = rc * 256 + 128 * h, sc = (g0 + rc) & 7;
         const uint32_t lanebase = ((uint32_t)(32 * q) << 16) + (uint32_t)(t * PRO_PTS / 2);
         for (int k = 0; k < nkb && !S.abort; ++k) {
-            const int s = k % NT, u = k / NT, sa = k & 1;
+            const int s = k % NT, u = k / NT, sa = k % NA;
             if (!mbar_wait(&S.tma_full[s], u & 1, wlim) ||
-                (k >= 2 && !mbar_wait(&S.kb_done[(k - 2) % NT], ((k - 2) / NT) & 1, wlim))) {
+                (k >= NA && !mbar_wait(&S.kb_done[(k - NA) % NT], ((k - NA) / NT) & 1, wlim))) {
                 set_abort(S, err, 8);
                 break;
             }
@@ -527,53 +534,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // every CC chunks, and at the end, E joins the running sum first
             if (nprod == 3 && ((c + 1) % CC == 0 || c == nch - 1)) {
                 for (uint32_t col = 0; col < N; col += 16) {
-                    uint32_t a[16], m[16];
+                    uint32_t a[16];
                     tmem_ld16(lanebase + COL_CORR + col, a);
-                    if (have_sum) tmem_ld16(lanebase + COL_SUM + col, m);
                     tmem_ld_wait();
-                    if (have_sum) {
 #pragma unroll
-                        for (int t = 0; t < 16; ++t)
-                            a[t] = __float_as_uint(__uint_as_float(m[t]) + __uint_as_float(a[t]));
+                    for (int t = 0; t < 16; ++t) {
+                        float& sm = S.sum[col + t][row];
+                        sm = have_sum ? sm + __uint_as_float(a[t]) : __uint_as_float(a[t]);
                     }
-                    tmem_st16(lanebase + COL_SUM + col, a);
                 }
-                tmem_st_wait();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.corr_empty);
                 have_sum = true;
             }
-            // D joins the running sum; the accumulator is released at once
+            // D joins the running sum; the accumulator is released as soon as it is read
             for (uint32_t col = 0; col < N; col += 16) {
-                uint32_t a[16], m[16];
+                uint32_t a[16];
                 tmem_ld16(lanebase + (uint32_t)j * COL_ACC + col, a);
-                if (have_sum) tmem_ld16(lanebase + COL_SUM + col, m);
                 tmem_ld_wait();
-                if (have_sum) {
-#pragma unroll
-                    for (int t = 0; t < 16; ++t) a[t] = __float_as_uint(__uint_as_float(m[t]) + __uint_as_float(a[t]));
+                if (col + 16 >= N) {   // the last read of this buffer: release it
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.acc_empty[j]);
                 }
-                tmem_st16(lanebase + COL_SUM + col, a);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    float& sm = S.sum[col + t][row];
+                    sm = have_sum ? sm + __uint_as_float(a[t]) : __uint_as_float(a[t]);
+                }
             }
-            tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.acc_empty[j]);
             if (flush) {
                 // the running sum to the CTA's FP64 slot, while the MMAs fill the other D buffer
-                for (uint32_t col = 0; col < N; col += 16) {
-                    uint32_t a[16];
-                    tmem_ld16(lanebase + COL_SUM + col, a);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        const double v = f32_ldexp_f64(__uint_as_float(a[t]), pexp + S.fexp[col + t]);
-                        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(dst + (size_t)(col + t) * TC_M), "d"(v)
-                                     : "memory");
-                    }
+                for (uint32_t col = 0; col < N; ++col) {
+                    const double v = f32_ldexp_f64(S.sum[col][row], pexp + S.fexp[col]);
+                    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(dst + (size_t)col * TC_M), "d"(v) : "memory");
                 }
-                tc_fence_before();
             }
         }
     }
