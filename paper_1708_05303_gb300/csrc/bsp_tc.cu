@@ -47,16 +47,19 @@ constexpr int TC_MAXSH = 64;     // F0 rows per tile
 // warps: 0 copies, 1 MMA, 4 .. 4 + N_PRO - 1 pair products (N_PRO / 4 per TMEM
 // lane quadrant, each a 64 / (N_PRO / 4)-point part of every K-block), then 4 drain warps
 constexpr int N_PRO = TC_PRO_WARPS, PRO_PTS = 64 / (N_PRO / 4), PRO_CH = PRO_PTS / 4;
-constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, W_EPI0 = W_PRO0 + N_PRO;
-constexpr int TC_THREADS = 32 * (W_EPI0 + 4);
+// 8 drain warps: warp 12 + 4 h + q reads columns [48 h, 48 h + 48) of lane
+// quadrant q and keeps their running sum in registers
+constexpr int W_TMA = 0, W_MMA = 1, W_PRO0 = 4, W_EPI0 = W_PRO0 + N_PRO, N_EPI = 8, EPI_COLS = 48;
+constexpr int TC_THREADS = 32 * (W_EPI0 + N_EPI);
 static_assert(N_PRO == 8 || N_PRO == 16, "pair-product warps: 8 or 16");
 // tensor memory columns: the P_hi F_hi accumulators D0 [0,96) and D1 [96,192),
 // drained every chunk; the correction accumulator E = P_hi F_lo + P_lo F_hi
 // [192,288), drained every CORR_KB K-blocks (its terms are ~2^-11 of D's, so
 // its own truncation stays far below D's); three A buffers [288,352),
 // [352,416), [416,480), hi in the first 32 columns, lo in the next 32.  The
-// running FP32 sum of the drained accumulators lives in shared memory, which
-// frees the tensor memory for the third A buffer: with two, the products of
+// running FP32 sum of the drained accumulators lives in the drain warps'
+// registers, which frees the tensor memory for the third A buffer: with two,
+// the products of
 // K-block k + 2 waited for the MMAs of K-block k to complete, and that chain,
 // not any one unit, set the pace (clock traces: ~2 050 cycles per K-block
 // with the tensor pipe ~20 % busy).
@@ -71,7 +74,6 @@ constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
 struct TcSmem {
     uint8_t f0[NT][TC_MAXSH * 256];        // [stage][row][64 floats], each half 128-byte swizzled
     uint8_t b[NT][TC_NMAX / 8 * 2048];     // [stage][group of 8 fields][hi 1024 B | lo 1024 B]
-    float sum[TC_NMAX][TC_M];              // running FP32 sum, [column][pair]
     // tma_full: a stage's copies landed; kb_done: the MMAs of K-block k finished
     // (frees TMA stage k % NT and A buffer k % NA); a_full: A buffer written
     // corr_empty: E was read
@@ -312,9 +314,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int j = 0; j < NA; ++j) mbar_init(&S.a_full[j], N_PRO);
         for (int j = 0; j < 2; ++j) {
             mbar_init(&S.acc_full[j], 1);
-            mbar_init(&S.acc_empty[j], 4);
+            mbar_init(&S.acc_empty[j], N_EPI);
         }
-        mbar_init(&S.corr_empty, 4);
+        mbar_init(&S.corr_empty, N_EPI);
         S.abort = 0;
         // field-plane copies: one per run of consecutive groups
         int npc = 0;
@@ -515,13 +517,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (lane == 0) mbar_arrive(&S.a_full[sa]);
         }
     } else if (warp >= W_EPI0) {
-        const int q = warp & 3;
+        const int q = warp & 3, hc = (warp - W_EPI0) >> 2;
         const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
         const int row = 32 * q + lane;
+        const uint32_t c0 = (uint32_t)(EPI_COLS * hc);   // this warp's columns [c0, c0 + 48) within N
         // the CTA's FP64 slot, [column][pair] (zeroed before the launch): the flushes are
         // fire-and-forget reductions, coalesced over the warp's 32 pairs
         double* dst = partial + (size_t)blockIdx.x * TC_SLOT + row;
         const int pexp = -ilogbf(S.pscale[row]);   // the scales are powers of two
+        float sum[EPI_COLS];
+#pragma unroll
+        for (int t = 0; t < EPI_COLS; ++t) sum[t] = 0.f;
         for (int c = 0; c < nch && !S.abort; ++c) {
             const int j = c & 1, g = c % FL;
             const bool flush = g == FL - 1 || c == nch - 1;
@@ -530,45 +536,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            bool have_sum = g > 0;
             // every CC chunks, and at the end, E joins the running sum first
             if (nprod == 3 && ((c + 1) % CC == 0 || c == nch - 1)) {
-                for (uint32_t col = 0; col < N; col += 16) {
-                    uint32_t a[16];
-                    tmem_ld16(lanebase + COL_CORR + col, a);
-                    tmem_ld_wait();
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        float& sm = S.sum[col + t][row];
-                        sm = have_sum ? sm + __uint_as_float(a[t]) : __uint_as_float(a[t]);
+                for (int cg = 0; cg < EPI_COLS / 16; ++cg) {
+                    const uint32_t col = c0 + 16u * cg;
+                    if (col < N) {
+                        uint32_t a[16];
+                        tmem_ld16(lanebase + COL_CORR + col, a);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) sum[16 * cg + t] += __uint_as_float(a[t]);
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.corr_empty);
-                have_sum = true;
             }
             // D joins the running sum; the accumulator is released as soon as it is read
-            for (uint32_t col = 0; col < N; col += 16) {
-                uint32_t a[16];
-                tmem_ld16(lanebase + (uint32_t)j * COL_ACC + col, a);
-                tmem_ld_wait();
-                if (col + 16 >= N) {   // the last read of this buffer: release it
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&S.acc_empty[j]);
-                }
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    float& sm = S.sum[col + t][row];
-                    sm = have_sum ? sm + __uint_as_float(a[t]) : __uint_as_float(a[t]);
+            for (int cg = 0; cg < EPI_COLS / 16; ++cg) {
+                const uint32_t col = c0 + 16u * cg;
+                if (col < N) {
+                    uint32_t a[16];
+                    tmem_ld16(lanebase + (uint32_t)j * COL_ACC + col, a);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) sum[16 * cg + t] += __uint_as_float(a[t]);
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.acc_empty[j]);
             if (flush) {
                 // the running sum to the CTA's FP64 slot, while the MMAs fill the other D buffer
-                for (uint32_t col = 0; col < N; ++col) {
-                    const double v = f32_ldexp_f64(S.sum[col][row], pexp + S.fexp[col]);
-                    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(dst + (size_t)col * TC_M), "d"(v) : "memory");
+#pragma unroll
+                for (int t = 0; t < EPI_COLS; ++t) {
+                    const uint32_t col = c0 + (uint32_t)t;
+                    if (col < N) {
+                        const double v = f32_ldexp_f64(sum[t], pexp + S.fexp[col]);
+                        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(dst + (size_t)col * TC_M), "d"(v)
+                                     : "memory");
+                    }
+                    sum[t] = 0.f;
                 }
             }
         }
