@@ -10,7 +10,7 @@
 //   warp 0      bulk copies (TMA engine, no tensor map): the F^0 rows (FP32)
 //               of the tile's shells and the hi/lo planes of its field
 //               groups, stored by the FFT as the swizzled shared-memory image
-//               (one copy per contiguous run), four stages deep;
+//               (one copy per contiguous run), five stages deep;
 //   warps 4-11  form P = F_b F_c in FP32 (one pair per TMEM lane, half a
 //               K-block per warp), split it into 16-bit hi + lo and store
 //               both in tensor memory, where the MMA reads its A operand;
@@ -39,7 +39,7 @@ constexpr int TC_M = 128;        // pairs per tile = MMA M
 constexpr int TC_NMAX = 96;      // field rows per tile = MMA N (max)
 constexpr int TC_SLOT = 128 * 128;   // FP64 values per CTA slot of the partial sums, [column][pair]
 constexpr int TC_KB = 64;        // x-points per K-block (128 bytes of 16-bit values)
-constexpr int NT = 4;            // TMA ring stages (F0 rows + field planes)
+constexpr int NT = 5;            // TMA ring stages (F0 rows + field planes)
 constexpr int TC_MAXSH = 64;     // F0 rows per tile
 #ifndef TC_PRO_WARPS
 #define TC_PRO_WARPS 8
