@@ -10,18 +10,19 @@
 //   warp 0      bulk copies (TMA engine, no tensor map): the F^0 rows (FP32)
 //               of the tile's shells and the hi/lo planes of its field
 //               groups, stored by the FFT as the swizzled shared-memory image
-//               (one copy per contiguous run), five stages deep;
+//               (one copy per contiguous run), four stages deep;
 //   warps 4-11  form P = F_b F_c in FP32 (one pair per TMEM lane, half a
 //               K-block per warp), split it into 16-bit hi + lo and store
 //               both in tensor memory, where the MMA reads its A operand;
-//   warp 1      one thread issues tcgen05.mma kind::f16, M=128, K=16, A from
+//   warp 1      walks the K-blocks (warp-uniform loop state); one elected
+//               lane issues tcgen05.mma kind::f16, M=128, K=16, A from
 //               tensor memory, B (field planes) from shared memory:
 //               D += P_hi F_hi and, in a separate accumulator, E += P_hi F_lo
 //               + P_lo F_hi (split products; D alone for the plain 16-bit
 //               mode), FP32 accumulators in tensor memory;
-//   warps 12-15 drain D every `chunk` K-blocks and E every CORR_KB K-blocks
-//               (tcgen05.ld), add them to a running FP32 sum in tensor
-//               memory, and every FLUSH_KB K-blocks add that sum, unscaled,
+//   warps 12-19 drain D every `chunk` K-blocks and E every CORR_KB K-blocks
+//               (tcgen05.ld), add them to a running FP32 sum in registers,
+//               and every FLUSH_KB K-blocks add that sum, unscaled,
 //               to the CTA's FP64 slot in global memory (fire-and-forget
 //               reductions).
 // Two accumulator buffers and two A buffers in tensor memory keep TMA, the
@@ -39,13 +40,13 @@ constexpr int TC_M = 128;        // pairs per tile = MMA M
 constexpr int TC_NMAX = 96;      // field rows per tile = MMA N (max)
 constexpr int TC_SLOT = 128 * 128;   // FP64 values per CTA slot of the partial sums, [column][pair]
 constexpr int TC_KB = 64;        // x-points per K-block (128 bytes of 16-bit values)
-constexpr int NT = 5;            // TMA ring stages (F0 rows + field planes)
+constexpr int NT = 4;            // TMA ring stages (F0 rows + field planes)
 constexpr int TC_MAXSH = 64;     // F0 rows per tile
 #ifndef TC_PRO_WARPS
 #define TC_PRO_WARPS 8
 #endif
 // warps: 0 copies, 1 MMA, 4 .. 4 + N_PRO - 1 pair products (N_PRO / 4 per TMEM
-// lane quadrant, each a 64 / (N_PRO / 4)-point part of every K-block), then 4 drain warps
+// lane quadrant, each a 64 / (N_PRO / 4)-point part of every K-block), then 8 drain warps
 constexpr int N_PRO = TC_PRO_WARPS, PRO_PTS = 64 / (N_PRO / 4), PRO_CH = PRO_PTS / 4;
 // 8 drain warps: warp 12 + 4 h + q reads columns [48 h, 48 h + 48) of lane
 // quadrant q and keeps their running sum in registers
@@ -54,19 +55,16 @@ constexpr int TC_THREADS = 32 * (W_EPI0 + N_EPI);
 static_assert(N_PRO == 8 || N_PRO == 16, "pair-product warps: 8 or 16");
 // tensor memory columns: the P_hi F_hi accumulators D0 [0,96) and D1 [96,192),
 // drained every chunk; the correction accumulator E = P_hi F_lo + P_lo F_hi
-// [192,288), drained every CORR_KB K-blocks (its terms are ~2^-11 of D's, so
-// its own truncation stays far below D's); three A buffers [288,352),
-// [352,416), [416,480), hi in the first 32 columns, lo in the next 32.  The
-// running FP32 sum of the drained accumulators lives in the drain warps'
-// registers, which frees the tensor memory for the third A buffer: with two,
-// the products of
-// K-block k + 2 waited for the MMAs of K-block k to complete, and that chain,
-// not any one unit, set the pace (clock traces: ~2 050 cycles per K-block
-// with the tensor pipe ~20 % busy).
+// [192,288), drained every CORR_KB K-blocks; two A buffers [288,352) and
+// [352,416), hi in the first 32 columns, lo in the next 32.  The running FP32
+// sum of the drained accumulators lives in the drain warps' registers.
 // E's terms are ~2^-11 of D's: kept apart, the tensor core's truncating FP32
-// accumulation no longer loses half an ulp of D on each correction product.
+// accumulation does not lose half an ulp of D on each correction product.
+// With the MMAs issued by an elected lane of the whole warp (below), the 12
+// MMAs of a split K-block issue in ~320 cycles and complete ~500 later, so a
+// third A buffer no longer shortens the chain products -> MMAs -> products.
 constexpr uint32_t TMEM_COLS = 512, COL_ACC = 96, COL_CORR = 192, COL_A = 288;
-constexpr int NA = 3;            // A buffers (pair products) in tensor memory
+constexpr int NA = 2;            // A buffers (pair products) in tensor memory
 constexpr int CORR_KB = 64;      // K-blocks per drain of E (a multiple of the chunk)
 constexpr int FLUSH_KB = 128;    // K-blocks between FP64 flushes of the running sum
 constexpr long long WAIT_CYCLES = 1ll << 33;   // ~4 s at 2 GHz
@@ -103,8 +101,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
-// Wait for the phase of parity `parity` to complete; false after ~4 s.
+// Has the phase of parity `parity` completed?  test_wait never blocks;
+// try_wait may block for a short time set by the hardware.
 __device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -114,22 +123,29 @@ __device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// Waits poll with a suspend-time hint: the waiting thread sleeps in the
-// barrier until the phase completes (or ~2 us pass) instead of re-reading
-// shared memory in a tight loop, which took shared-memory bandwidth from the
-// copies, the pair products and the MMAs.
+// Wait for the phase of parity `parity` to complete; false once `limit` cycles
+// have passed (~4 s by default).  After one plain try_wait, waits poll with a
+// suspend-time hint: the waiting thread sleeps in the barrier until the phase
+// completes (or ~2 us pass) instead of re-reading shared memory in a tight
+// loop, which took shared-memory bandwidth from the copies, the pair products
+// and the MMAs.  Under a short limit (< 2^20 cycles) the wait polls with
+// test_wait instead, so that the limit holds to within a few hundred cycles.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit = WAIT_CYCLES) {
     const uint32_t addr = smem_u32(b);
-    if (mbar_test(addr, parity)) return true;
+    const bool sleep = limit >= (1ll << 20);
+    if (sleep ? mbar_try(addr, parity) : mbar_test(addr, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(addr), "r"(parity), "r"(2000u)
-            : "memory");
+        if (sleep)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+                " selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(addr), "r"(parity), "r"(2000u)
+                : "memory");
+        else
+            done = mbar_test(addr, parity);
         if (done) return true;
         if (clock64() - t0 > limit) return false;
     }
@@ -153,6 +169,18 @@ __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint3
         " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
         "r"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
+}
+__device__ __forceinline__ void mma_ts2(uint32_t d, uint32_t a, uint32_t blo, uint32_t bhi, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n .reg .b64 bd;\n setp.ne.b32 p, %5, 0;\n mov.b64 bd, {%2, %3};\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], bd, %4, p;\n}\n" ::"r"(d),
+        "r"(a), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ bool elect_one() {
+    uint32_t e;
+    asm volatile("{\n .reg .b32 r;\n .reg .pred p;\n elect.sync r|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n" : "=r"(e));
+    return e != 0;
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -411,51 +439,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!mbar_wait(&S.tma_full[k % NT], (k / NT) & 1)) atomicOr(err, 16);
         }
     } else if (warp == W_MMA) {
-        if (lane == 0) {
-            const uint32_t idesc = make_idesc(F16 ? 0u : 1u, N);
-            const uint32_t b0 = smem_u32(S.b[0]);
-            int done = 0, kc = 0, c = 0;   // kc = k % CHUNK, c = k / CHUNK
-            for (int k = 0; k < nkb; ++k) {
-                const int s = k % NT, u = k / NT, sa = k % NA;
-                const int j = c & 1;
-                const bool efirst = kc == 0 && c % CC == 0;   // first K-block of a drain period of E
-                if (kc == 0 && c >= 2 && !mbar_wait(&S.acc_empty[j], ((c >> 1) - 1) & 1, wlim)) {
-                    set_abort(S, err, 2);
-                    break;
-                }
-                if (nprod == 3 && efirst && c > 0 && !mbar_wait(&S.corr_empty, ((c / CC) - 1) & 1, wlim)) {
-                    set_abort(S, err, 2);
-                    break;
-                }
-                if (!mbar_wait(&S.tma_full[s], u & 1, wlim) || !mbar_wait(&S.a_full[sa], (k / NA) & 1, wlim)) {
-                    set_abort(S, err, 4);
-                    break;
-                }
-                if (S.abort) break;
-                tc_fence_after();
+        // the whole warp walks the K-blocks (the loop state stays warp-uniform);
+        // one elected lane issues the MMAs and commits
+        const uint32_t idesc = make_idesc(F16 ? 0u : 1u, N);
+        // B descriptors: the high word is fixed (stride, version, swizzle), the low
+        // word is the start address >> 4: stage s, slice kk, half h at
+        // dlo0 + s * (stage bytes >> 4) + 2 kk + 64 h
+        const uint32_t dhi = (uint32_t)(sw128_desc(0u, 2048) >> 32);
+        const uint32_t dlo0 = (uint32_t)sw128_desc(smem_u32(S.b[0]), 2048);
+        constexpr uint32_t STAGE16 = (uint32_t)(sizeof(S.b[0]) >> 4);
+        int done = 0, kc = 0, c = 0;   // kc = k % CHUNK, c = k / CHUNK
+        bool ok = true;
+        for (int k = 0; k < nkb; ++k) {
+            const int s = k % NT, u = k / NT, sa = k % NA;
+            const int j = c & 1;
+            const bool efirst = kc == 0 && c % CC == 0;   // first K-block of a drain period of E
+            if (kc == 0 && c >= 2 && !__all_sync(0xffffffffu, mbar_wait(&S.acc_empty[j], ((c >> 1) - 1) & 1, wlim))) {
+                ok = false;
+                break;
+            }
+            if (nprod == 3 && efirst && c > 0 &&
+                !__all_sync(0xffffffffu, mbar_wait(&S.corr_empty, ((c / CC) - 1) & 1, wlim))) {
+                ok = false;
+                break;
+            }
+            if (!__all_sync(0xffffffffu, mbar_wait(&S.tma_full[s], u & 1, wlim) && mbar_wait(&S.a_full[sa], (k / NA) & 1, wlim))) {
+                if (lane == 0) set_abort(S, err, 4);
+                break;
+            }
+            if (__shfl_sync(0xffffffffu, S.abort, 0)) break;
+            tc_fence_after();
+            if (elect_one()) {
                 const uint32_t d = tmem + (uint32_t)j * COL_ACC, de = tmem + COL_CORR;
                 const uint32_t ah = tmem + COL_A + (uint32_t)sa * 64, al = ah + 32;
-                const uint32_t bh = b0 + (uint32_t)s * (uint32_t)sizeof(S.b[0]), bl = bh + 1024;
+                const uint32_t lh = dlo0 + (uint32_t)s * STAGE16;
 #pragma unroll
                 for (int kk = 0; kk < TC_KB / 16; ++kk) {
-                    const uint32_t o = (uint32_t)kk * 32, oa = (uint32_t)kk * 8;
-                    mma_ts(d, ah + oa, sw128_desc(bh + o, 2048), idesc, (kc == 0 && kk == 0) ? 0u : 1u);
+                    const uint32_t oa = (uint32_t)kk * 8, ob = (uint32_t)kk * 2;
+                    mma_ts2(d, ah + oa, lh + ob, dhi, idesc, (kc == 0 && kk == 0) ? 0u : 1u);
                     if (nprod == 3) {
-                        mma_ts(de, ah + oa, sw128_desc(bl + o, 2048), idesc, (efirst && kk == 0) ? 0u : 1u);
-                        mma_ts(de, al + oa, sw128_desc(bh + o, 2048), idesc, 1u);
+                        mma_ts2(de, ah + oa, lh + 64u + ob, dhi, idesc, (efirst && kk == 0) ? 0u : 1u);
+                        mma_ts2(de, al + oa, lh + ob, dhi, idesc, 1u);
                     }
                 }
                 mma_commit(&S.kb_done[s]);
-                if (++kc == CHUNK || k == nkb - 1) {
-                    mma_commit(&S.acc_full[j]);
-                    kc = 0;
-                    ++c;
-                }
-                done = k + 1;
+                if (kc + 1 == CHUNK || k == nkb - 1) mma_commit(&S.acc_full[j]);
             }
-            // the last MMAs must finish before tensor memory is released (long limit)
-            if (done > 0 && !mbar_wait(&S.kb_done[(done - 1) % NT], ((done - 1) / NT) & 1)) atomicOr(err, 32);
+            __syncwarp();
+            if (++kc == CHUNK || k == nkb - 1) {
+                kc = 0;
+                ++c;
+            }
+            done = k + 1;
         }
+        if (!ok && lane == 0) set_abort(S, err, 2);
+        // the last MMAs must finish before tensor memory is released (long limit)
+        if (done > 0 && !__all_sync(0xffffffffu, mbar_wait(&S.kb_done[(done - 1) % NT], ((done - 1) / NT) & 1)) && lane == 0)
+            atomicOr(err, 32);
     } else if (warp >= W_PRO0 && warp < W_PRO0 + N_PRO) {
         // lane quadrant q of tensor memory = pairs 32 q .. 32 q + 31; part t of each
         // K-block: points t * PRO_PTS .., 16-byte chunks j0 .. j0 + PRO_CH - 1 of F0 half h
