@@ -23,6 +23,7 @@
 // buffers with one barrier per stage.  Twiddles come from a host table of
 // exp(+2 pi i t/N) computed in FP64.
 #include <algorithm>
+#include <type_traits>
 
 #include "bsp_internal.h"
 
@@ -357,48 +358,15 @@ __global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restri
     }
 }
 
-// Pass 3: real inverse DFT along z for P consecutive y of one x, through a
-// complex DFT of length M = N/2:  Z_k = (H_k + conj H_{M-k})
-//   + i (H_k - conj H_{M-k}) e^{2 pi i k/N},  F[2m] = Re z_m, F[2m+1] = Im z_m,
-// with Im H_0 = Im H_M = 0 (the Hermitian part of the n_z = 0, N/2 planes).
-template <typename R, int P, int NN>
-__global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restrict__ t2,
-                                                size_t t2_stride, const cx<R>* __restrict__ twg,
-                                                const FieldDesc* __restrict__ fields, R* __restrict__ out,
-                                                size_t out_stride, uint32_t* __restrict__ hi,
-                                                uint32_t* __restrict__ lo, int f16,
-                                                const unsigned* __restrict__ fmax2,
-                                                unsigned* __restrict__ f0max, FieldLayout lay) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = NN ? NN : g.n, M = N / 2;
-    cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
-    cx<R>* buf = tw + N;
-    cx<R>* scr = buf + smem_elems<false, P>(M);
-    const int nyb = (N + P - 1) / P;
-    const int x = blockIdx.x / nyb, y0 = (blockIdx.x % nyb) * P;
-    const cx<R>* src = t2 + (size_t)blockIdx.y * t2_stride;
-    for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
-    __syncthreads();
-    for (int e = threadIdx.x; e < M * P; e += NTHR) {
-        const int k = e % M, p = e / M, y = y0 + p;
-        cx<R> z = {(R)0, (R)0};
-        if (y < N) {
-            const cx<R>* h = src + ((size_t)x * N + y) * g.nKz;
-            cx<R> a = {(R)0, (R)0}, b = {(R)0, (R)0};
-            if (k < g.nKz) a = h[k];
-            if (M - k < g.nKz) b = h[M - k];
-            if (k == 0) { a.im = (R)0; b.im = (R)0; }   // H_0 and H_M: real parts only
-            const cx<R> bc = {b.re, -b.im};
-            const cx<R> s = cadd(a, bc), d = csub(a, bc);
-            z = cadd(s, cmuli(cmul(d, tw[k])));
-        }
-        buf[sidx<false, P>(p, k, M)] = z;
-    }
-    __syncthreads();
-    const cx<R>* res;
-    if constexpr (NN > 0) res = fft_ct<R, false, P, NN / 2>(buf, scr, tw, 2);
-    else res = fft_pingpong<R, false, P>(buf, scr, M, g.rad_h, g.nrad_h, tw, 2);
-    const FieldDesc fd = fields[blockIdx.y];
+// Output of pass 3 for P consecutive y of one x: the real values of each
+// z-line, res[sidx<false, P>(p, m, M)] = F[2m] + i F[2m+1], scaled and
+// written as the field's FP32 row and/or 16-bit hi/lo planes.
+template <typename R, int P>
+__device__ __forceinline__ void pass3_store(const FftGeom& g, int N, int M, int x, int y0, const cx<R>* res,
+                                            const FieldDesc& fd, R* __restrict__ out, size_t out_stride,
+                                            uint32_t* __restrict__ hi, uint32_t* __restrict__ lo, int f16,
+                                            const unsigned* __restrict__ fmax2, unsigned* __restrict__ f0max,
+                                            FieldLayout lay) {
     const bool kbm = lay.groups16 > 0;
     R* dst = fd.out32 >= 0 ? out + (kbm ? (size_t)0 : (size_t)fd.out32 * out_stride) : nullptr;
     const size_t plane = (size_t)N * N * M;   // 32-bit words (two 16-bit values) per field plane
@@ -520,6 +488,111 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
     if (f0max && dst) block_max_to(f0max + fd.out32, mx);
 }
 
+// Pass 3: real inverse DFT along z for P consecutive y of one x, through a
+// complex DFT of length M = N/2:  Z_k = (H_k + conj H_{M-k})
+//   + i (H_k - conj H_{M-k}) e^{2 pi i k/N},  F[2m] = Re z_m, F[2m+1] = Im z_m,
+// with Im H_0 = Im H_M = 0 (the Hermitian part of the n_z = 0, N/2 planes).
+template <typename R, int P, int NN>
+__global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restrict__ t2,
+                                                size_t t2_stride, const cx<R>* __restrict__ twg,
+                                                const FieldDesc* __restrict__ fields, R* __restrict__ out,
+                                                size_t out_stride, uint32_t* __restrict__ hi,
+                                                uint32_t* __restrict__ lo, int f16,
+                                                const unsigned* __restrict__ fmax2,
+                                                unsigned* __restrict__ f0max, FieldLayout lay) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = NN ? NN : g.n, M = N / 2;
+    cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
+    cx<R>* buf = tw + N;
+    cx<R>* scr = buf + smem_elems<false, P>(M);
+    const int nyb = (N + P - 1) / P;
+    const int x = blockIdx.x / nyb, y0 = (blockIdx.x % nyb) * P;
+    const cx<R>* src = t2 + (size_t)blockIdx.y * t2_stride;
+    for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
+    __syncthreads();
+    for (int e = threadIdx.x; e < M * P; e += NTHR) {
+        const int k = e % M, p = e / M, y = y0 + p;
+        cx<R> z = {(R)0, (R)0};
+        if (y < N) {
+            const cx<R>* h = src + ((size_t)x * N + y) * g.nKz;
+            cx<R> a = {(R)0, (R)0}, b = {(R)0, (R)0};
+            if (k < g.nKz) a = h[k];
+            if (M - k < g.nKz) b = h[M - k];
+            if (k == 0) { a.im = (R)0; b.im = (R)0; }   // H_0 and H_M: real parts only
+            const cx<R> bc = {b.re, -b.im};
+            const cx<R> s = cadd(a, bc), d = csub(a, bc);
+            z = cadd(s, cmuli(cmul(d, tw[k])));
+        }
+        buf[sidx<false, P>(p, k, M)] = z;
+    }
+    __syncthreads();
+    const cx<R>* res;
+    if constexpr (NN > 0) res = fft_ct<R, false, P, NN / 2>(buf, scr, tw, 2);
+    else res = fft_pingpong<R, false, P>(buf, scr, M, g.rad_h, g.nrad_h, tw, 2);
+    pass3_store<R, P>(g, N, M, x, y0, res, fields[blockIdx.y], out, out_stride, hi, lo, f16, fmax2, f0max, lay);
+}
+
+// Pass 3 for n = 512 (M = 256 = 16 x 16) with the z-lines in registers:
+// 16 threads per line, P3R = 16 lines (consecutive y of one x) per CTA.
+// With k = k1 + 16 k2 and m = m1 + 16 m2,
+//   z_m = sum_k1 W16^{k1 m2} [ W256^{k1 m1} sum_k2 Z_{k1 + 16 k2} W16^{k2 m1} ],
+// W_L = e^{2 pi i / L}: thread k1 forms its 16 inputs Z_{k1 + 16 k2} straight
+// from T2 (the same Z_k as k_pass3), takes the inner 16-point DFT and the
+// twiddle in registers, the lines pass once through shared memory
+// (transposed), and thread m1 takes the outer 16-point DFT.  Two barriers
+// instead of one per Stockham stage, and every thread busy in both DFTs.
+constexpr int P3R = 16;
+constexpr int P3R_TS = 16 * 17;   // transpose rows per line: 16 rows of 16 + 1 pad
+constexpr size_t p3r_smem_bytes() {
+    return sizeof(cx<float>) * (512 + (size_t)smem_elems<false, P3R>(256));
+}
+static_assert(P3R * P3R_TS <= smem_elems<false, P3R>(256), "transpose fits in the output buffer");
+
+__global__ void __launch_bounds__(NTHR) k_pass3r(FftGeom g, const cx<float>* __restrict__ t2, size_t t2_stride,
+                                                 const cx<float>* __restrict__ twg,
+                                                 const FieldDesc* __restrict__ fields, float* __restrict__ out,
+                                                 size_t out_stride, uint32_t* __restrict__ hi,
+                                                 uint32_t* __restrict__ lo, int f16,
+                                                 const unsigned* __restrict__ fmax2,
+                                                 unsigned* __restrict__ f0max, FieldLayout lay) {
+    constexpr int N = 512, M = 256;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+    cx<float>* buf = tw + N;
+    const int x = blockIdx.x / (N / P3R), y0 = (blockIdx.x % (N / P3R)) * P3R;
+    const int p = threadIdx.x >> 4, t = threadIdx.x & 15;
+    for (int i = threadIdx.x; i < N; i += NTHR) tw[i] = twg[i];
+    __syncthreads();
+    const int nKz = g.nKz;
+    const cx<float>* h = t2 + (size_t)blockIdx.y * t2_stride + ((size_t)x * N + y0 + p) * nKz;
+    cx<float> v[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+        const int k = t + 16 * k2;
+        cx<float> a = {0.f, 0.f}, b = {0.f, 0.f};
+        if (k < nKz) a = h[k];
+        if (M - k < nKz) b = h[M - k];
+        if (k == 0) { a.im = 0.f; b.im = 0.f; }   // H_0 and H_M: real parts only
+        const cx<float> bc = {b.re, -b.im};
+        const cx<float> s = cadd(a, bc), d = csub(a, bc);
+        v[k2] = cadd(s, cmuli(cmul(d, tw[k])));
+    }
+    butterfly<float, 16>(v);   // v[m1] = sum_k2 Z_{t + 16 k2} W16^{k2 m1}
+    cx<float>* tr = buf + p * P3R_TS;
+#pragma unroll
+    for (int m1 = 0; m1 < 16; ++m1) tr[m1 * 17 + t] = m1 == 0 ? v[0] : cmul(v[m1], tw[2 * t * m1]);   // W256^{t m1}
+    __syncthreads();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) v[k1] = tr[t * 17 + k1];
+    butterfly<float, 16>(v);   // v[m2] = z_{t + 16 m2}
+    __syncthreads();           // every line's transpose is read before the output layout reuses it
+#pragma unroll
+    for (int m2 = 0; m2 < 16; ++m2) buf[sidx<false, P3R>(p, t + 16 * m2, M)] = v[m2];
+    __syncthreads();
+    pass3_store<float, P3R>(g, N, M, x, y0, buf, fields[blockIdx.y], out, out_stride, hi, lo, f16, fmax2, f0max,
+                            lay);
+}
+
 template <typename R>
 struct FftCfg;
 template <>
@@ -566,8 +639,21 @@ cudaError_t launch_n(const FftGeom& g, const cx<float>* delta, const int16_t* sh
     dim3 g1(g.nK * nkzb, nfields), g2(N * nkzb, nfields), g3(N * ((N + C::P3 - 1) / C::P3), nfields);
     k_pass1<R, C::P, NN><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);
     k_pass2<R, C::P, NN><<<g2, NTHR, sm12, st>>>(g, t1, t1_stride, tw, t2, t2_stride, d_fields, fmax2);
-    k_pass3<R, C::P3, NN><<<g3, NTHR, sm3, st>>>(g, t2, t2_stride, tw, d_fields, out, out_stride, hi, lo, f16,
-                                                 fmax2, f0max, lay);
+    if constexpr (NN == 512 && std::is_same<R, float>::value) {
+        static bool set3r = false;
+        if (!set3r) {
+            if ((e = cudaFuncSetAttribute(k_pass3r, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)p3r_smem_bytes())) != cudaSuccess)
+                return e;
+            set3r = true;
+        }
+        k_pass3r<<<dim3(N * (N / P3R), nfields), NTHR, p3r_smem_bytes(), st>>>(g, t2, t2_stride, tw, d_fields, out,
+                                                                               out_stride, hi, lo, f16, fmax2,
+                                                                               f0max, lay);
+    } else {
+        k_pass3<R, C::P3, NN><<<g3, NTHR, sm3, st>>>(g, t2, t2_stride, tw, d_fields, out, out_stride, hi, lo, f16,
+                                                     fmax2, f0max, lay);
+    }
     return cudaGetLastError();
 }
 
