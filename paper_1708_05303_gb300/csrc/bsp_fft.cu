@@ -358,6 +358,79 @@ __global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restri
     }
 }
 
+// Pass 2 for n = 512 with the y-lines in registers: 8 lines (consecutive
+// f_z of one x) per CTA, 32 threads per line, k_z fastest across the lanes so
+// that every global load and store is a run of 8 consecutive f_z (64 bytes).
+// With k = k1 + 32 k2 (thread k1 holds k2 = 0..15) and m = m1 + 16 m2,
+//   z_m = sum_k1 W32^{k1 m2} [ W512^{k1 m1} sum_k2 X_{k1 + 32 k2} W16^{k2 m1} ],
+// W_L = e^{2 pi i / L}; after one shared-memory transpose the outer 32-point
+// DFT over k1 = j1 + 2 j2 is a 16-point DFT over j2 in each of two threads
+// (j1 = 0, 1) and a radix-2 step between them through a shuffle:
+//   z_{m1 + 16 (n + 16 q)} = U_0[n] + (-1)^q W32^n U_1[n].
+constexpr int P2R = 8;
+__host__ __device__ constexpr int p2r_idx(int row, int p) { return row * P2R + p + (row >> 4) * 8; }   // row = k1 * 16 + m1
+constexpr size_t p2r_smem_bytes() { return sizeof(cx<float>) * (512 + (size_t)p2r_idx(511, P2R - 1) + 1); }
+
+__global__ void __launch_bounds__(NTHR) k_pass2r(FftGeom g, const cx<float>* __restrict__ t1, size_t t1_stride,
+                                                 const cx<float>* __restrict__ twg, cx<float>* __restrict__ t2,
+                                                 size_t t2_stride, const FieldDesc* __restrict__ fields,
+                                                 unsigned* __restrict__ fmax2) {
+    constexpr int N = 512;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+    cx<float>* tr = tw + N;
+    const int nkzb = (g.nKz + P2R - 1) / P2R;
+    const int x = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P2R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = lane & 7, c = lane >> 3;   // line (f_z offset) and lane group
+    const int kz = kz0 + p;
+    const bool live = kz < g.nKz;
+    for (int i = threadIdx.x; i < N; i += NTHR) tw[i] = twg[i];
+    const cx<float>* src = t1 + (size_t)blockIdx.y * t1_stride;
+    // step A: thread k1 = 4 warp + c
+    const int k1 = 4 * warp + c;
+    cx<float> v[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+        const int iy = k1 + 32 * k2, fy = iy < N / 2 ? iy : iy - N;
+        cx<float> val = {0.f, 0.f};
+        if (live && (!g.pruned || (fy >= -g.K && fy <= g.K))) {
+            const int cy = g.pruned ? fy + g.K : iy;
+            val = src[((size_t)cy * N + x) * g.nKz + kz];
+        }
+        v[k2] = val;
+    }
+    __syncthreads();   // twiddles
+    butterfly<float, 16>(v);   // v[m1] = sum_k2 X_{k1 + 32 k2} W16^{k2 m1}
+#pragma unroll
+    for (int m1 = 0; m1 < 16; ++m1) tr[p2r_idx(k1 * 16 + m1, p)] = m1 == 0 ? v[0] : cmul(v[m1], tw[k1 * m1]);
+    __syncthreads();
+    // step B: thread (m1 = 2 warp + (c >> 1), j1 = c & 1)
+    const int m1 = 2 * warp + (c >> 1), j1 = c & 1;
+#pragma unroll
+    for (int j2 = 0; j2 < 16; ++j2) v[j2] = tr[p2r_idx((j1 + 2 * j2) * 16 + m1, p)];
+    butterfly<float, 16>(v);   // U_j1[n]
+    cx<float>* dst = t2 + (size_t)blockIdx.y * t2_stride;
+    float mx = 0.f;
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+        cx<float> u = v[n];
+        if (j1) u = cmul(u, tw[16 * n]);   // W32^n U_1[n]
+        const cx<float> o = {__shfl_xor_sync(0xffffffffu, u.re, 8), __shfl_xor_sync(0xffffffffu, u.im, 8)};
+        // j1 = 0 keeps U_0 + W U_1 (m2 = n), j1 = 1 keeps U_0 - W U_1 (m2 = n + 16)
+        const cx<float> z = j1 ? csub(o, u) : cadd(u, o);
+        const int y = m1 + 16 * (n + 16 * j1);
+        if (live) {
+            dst[((size_t)x * N + y) * g.nKz + kz] = z;
+            mx = fmaxf(mx, fabsf(z.re) + fabsf(z.im));
+        }
+    }
+    if (fmax2) {
+        const int f = fields[blockIdx.y].out16;
+        if (f >= 0) block_max_to(fmax2 + f, mx);
+    }
+}
+
 // Output of pass 3 for P consecutive y of one x: the real values of each
 // z-line, res[sidx<false, P>(p, m, M)] = F[2m] + i F[2m+1], scaled and
 // written as the field's FP32 row and/or 16-bit hi/lo planes.
@@ -638,7 +711,19 @@ cudaError_t launch_n(const FftGeom& g, const cx<float>* delta, const int16_t* sh
     const int nkzb = (g.nKz + C::P - 1) / C::P;
     dim3 g1(g.nK * nkzb, nfields), g2(N * nkzb, nfields), g3(N * ((N + C::P3 - 1) / C::P3), nfields);
     k_pass1<R, C::P, NN><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);
-    k_pass2<R, C::P, NN><<<g2, NTHR, sm12, st>>>(g, t1, t1_stride, tw, t2, t2_stride, d_fields, fmax2);
+    if constexpr (NN == 512 && std::is_same<R, float>::value) {
+        static bool set2r = false;
+        if (!set2r) {
+            if ((e = cudaFuncSetAttribute(k_pass2r, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)p2r_smem_bytes())) != cudaSuccess)
+                return e;
+            set2r = true;
+        }
+        k_pass2r<<<dim3(N * ((g.nKz + P2R - 1) / P2R), nfields), NTHR, p2r_smem_bytes(), st>>>(
+            g, t1, t1_stride, tw, t2, t2_stride, d_fields, fmax2);
+    } else {
+        k_pass2<R, C::P, NN><<<g2, NTHR, sm12, st>>>(g, t1, t1_stride, tw, t2, t2_stride, d_fields, fmax2);
+    }
     if constexpr (NN == 512 && std::is_same<R, float>::value) {
         static bool set3r = false;
         if (!set3r) {
