@@ -235,6 +235,43 @@ __device__ __forceinline__ R filter_weight(const FieldDesc& fd, int n2, int fz, 
     return base * (R)1.125 * (((R)35 * mu2 - (R)30) * mu2 + (R)3);                     // 9 L_4
 }
 
+// Input of pass 1: the filtered spectrum W_f(n) S_f(n) at (f_x of ix, f_y of
+// iy, k_z), zero outside the pruned range.
+template <typename R>
+__device__ __forceinline__ cx<R> pass1_input(const FftGeom& g, const FieldDesc& fd, const cx<float>* __restrict__ delta,
+                                             const int16_t* __restrict__ shell_of, const float* __restrict__ radial,
+                                             int N, int ix, int fy, int iy, int kz) {
+    const int fx = freq_of(ix, N);
+    cx<R> val = {(R)0, (R)0};
+    if (kz < g.nKz && (!g.pruned || (fx >= -g.K && fx <= g.K))) {
+        const int fz = (kz == N / 2) ? -(N / 2) : kz;
+        const int n2 = fx * fx + fy * fy + fz * fz;
+        const R w = filter_weight<R>(fd, n2, fz, shell_of, radial, g.n2max);
+        if (w != (R)0) {
+            if (fd.kind == FIELD_UNIT) {
+                val.re = w;
+            } else {
+                const cx<float> d = delta[((size_t)ix * N + iy) * (N / 2 + 1) + kz];
+                if (fd.kind == FIELD_POWER) {
+                    // |delta|^2 of the Hermitian part: on the n_z = 0 and n/2 planes the
+                    // half spectrum holds both n and -n, (delta(n) + conj delta(-n)) / 2
+                    R re = (R)d.re, im = (R)d.im;
+                    if (kz == 0 || kz == N / 2) {
+                        const cx<float> m = delta[((size_t)((N - ix) % N) * N + (N - iy) % N) * (N / 2 + 1) + kz];
+                        re = (R)0.5 * (re + (R)m.re);
+                        im = (R)0.5 * (im - (R)m.im);
+                    }
+                    val.re = w * (re * re + im * im);
+                } else {
+                    val.re = w * (R)d.re;
+                    val.im = w * (R)d.im;
+                }
+            }
+        }
+    }
+    return val;
+}
+
 // Pass 1: filter + inverse DFT along x for P consecutive f_z of one f_y.
 template <typename R, int P, int NN>
 __global__ void __launch_bounds__(NTHR) k_pass1(FftGeom g, const cx<float>* __restrict__ delta,
@@ -256,34 +293,7 @@ __global__ void __launch_bounds__(NTHR) k_pass1(FftGeom g, const cx<float>* __re
     for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
     for (int e = threadIdx.x; e < N * P; e += NTHR) {
         const int p = e % P, ix = e / P, kz = kz0 + p;
-        const int fx = freq_of(ix, N);
-        cx<R> val = {(R)0, (R)0};
-        if (kz < g.nKz && (!g.pruned || (fx >= -g.K && fx <= g.K))) {
-            const int fz = (kz == N / 2) ? -(N / 2) : kz;
-            const int n2 = fx * fx + fy * fy + fz * fz;
-            const R w = filter_weight<R>(fd, n2, fz, shell_of, radial, g.n2max);
-            if (w != (R)0) {
-                if (fd.kind == FIELD_UNIT) {
-                    val.re = w;
-                } else {
-                    const cx<float> d = delta[((size_t)ix * N + iy) * (N / 2 + 1) + kz];
-                    if (fd.kind == FIELD_POWER) {
-                        // |delta|^2 of the Hermitian part: on the n_z = 0 and n/2 planes the
-                        // half spectrum holds both n and -n, (delta(n) + conj delta(-n)) / 2
-                        R re = (R)d.re, im = (R)d.im;
-                        if (kz == 0 || kz == N / 2) {
-                            const cx<float> m = delta[((size_t)((N - ix) % N) * N + (N - iy) % N) * (N / 2 + 1) + kz];
-                            re = (R)0.5 * (re + (R)m.re);
-                            im = (R)0.5 * (im - (R)m.im);
-                        }
-                        val.re = w * (re * re + im * im);
-                    } else {
-                        val.re = w * (R)d.re;
-                        val.im = w * (R)d.im;
-                    }
-                }
-            }
-        }
+        const cx<R> val = pass1_input<R>(g, fd, delta, shell_of, radial, N, ix, fy, iy, kz);
         buf[sidx<true, P>(p, ix, N)] = val;
     }
     __syncthreads();
@@ -371,6 +381,66 @@ constexpr int P2R = 8;
 __host__ __device__ constexpr int p2r_idx(int row, int p) { return row * P2R + p + (row >> 4) * 8; }   // row = k1 * 16 + m1
 constexpr size_t p2r_smem_bytes() { return sizeof(cx<float>) * (512 + (size_t)p2r_idx(511, P2R - 1) + 1); }
 
+// The 512-point inverse DFT of the CTA's 8 lines.  On entry thread (k1 = 4 warp
+// + c, line p) holds X_{k1 + 32 k2} in v[k2] and the twiddles are in tw; on
+// return thread (m1 = 2 warp + (c >> 1), j1 = c & 1, line p) holds
+// z_{m1 + 16 (n + 16 j1)} in v[n].  tr: the transpose buffer.
+__device__ __forceinline__ void line512(cx<float> (&v)[16], const cx<float>* tw, cx<float>* tr, int warp, int c,
+                                        int p) {
+    const int k1 = 4 * warp + c;
+    butterfly<float, 16>(v);   // v[m1] = sum_k2 X_{k1 + 32 k2} W16^{k2 m1}
+#pragma unroll
+    for (int m1 = 0; m1 < 16; ++m1) tr[p2r_idx(k1 * 16 + m1, p)] = m1 == 0 ? v[0] : cmul(v[m1], tw[k1 * m1]);
+    __syncthreads();
+    const int m1 = 2 * warp + (c >> 1), j1 = c & 1;
+#pragma unroll
+    for (int j2 = 0; j2 < 16; ++j2) v[j2] = tr[p2r_idx((j1 + 2 * j2) * 16 + m1, p)];
+    butterfly<float, 16>(v);   // U_j1[n]
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+        cx<float> u = v[n];
+        if (j1) u = cmul(u, tw[16 * n]);   // W32^n U_1[n]
+        const cx<float> o = {__shfl_xor_sync(0xffffffffu, u.re, 8), __shfl_xor_sync(0xffffffffu, u.im, 8)};
+        // j1 = 0 keeps U_0 + W U_1 (m2 = n), j1 = 1 keeps U_0 - W U_1 (m2 = n + 16)
+        v[n] = j1 ? csub(o, u) : cadd(u, o);
+    }
+}
+
+// Pass 1 for n = 512 with the x-lines in registers: 8 lines (consecutive
+// f_z of one f_y) per CTA, laid out and transformed as in k_pass2r.
+__global__ void __launch_bounds__(NTHR) k_pass1r(FftGeom g, const cx<float>* __restrict__ delta,
+                                                 const int16_t* __restrict__ shell_of,
+                                                 const float* __restrict__ radial,
+                                                 const FieldDesc* __restrict__ fields,
+                                                 const cx<float>* __restrict__ twg, cx<float>* __restrict__ t1,
+                                                 size_t t1_stride) {
+    constexpr int N = 512;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+    cx<float>* tr = tw + N;
+    const FieldDesc fd = fields[blockIdx.y];
+    const int nkzb = (g.nKz + P2R - 1) / P2R;
+    const int cy = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P2R;
+    const int fy = g.pruned ? cy - g.K : freq_of(cy, N);
+    const int iy = (fy + N) % N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = lane & 7, c = lane >> 3;
+    const int kz = kz0 + p;
+    for (int i = threadIdx.x; i < N; i += NTHR) tw[i] = twg[i];
+    const int k1 = 4 * warp + c;
+    cx<float> v[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) v[k2] = pass1_input<float>(g, fd, delta, shell_of, radial, N, k1 + 32 * k2, fy, iy, kz);
+    __syncthreads();   // twiddles
+    line512(v, tw, tr, warp, c, p);
+    const int m1 = 2 * warp + (c >> 1), j1 = c & 1;
+    if (kz < g.nKz) {
+        cx<float>* dst = t1 + (size_t)blockIdx.y * t1_stride;
+#pragma unroll
+        for (int n = 0; n < 16; ++n) dst[((size_t)cy * N + m1 + 16 * (n + 16 * j1)) * g.nKz + kz] = v[n];
+    }
+}
+
 __global__ void __launch_bounds__(NTHR) k_pass2r(FftGeom g, const cx<float>* __restrict__ t1, size_t t1_stride,
                                                  const cx<float>* __restrict__ twg, cx<float>* __restrict__ t2,
                                                  size_t t2_stride, const FieldDesc* __restrict__ fields,
@@ -401,28 +471,16 @@ __global__ void __launch_bounds__(NTHR) k_pass2r(FftGeom g, const cx<float>* __r
         v[k2] = val;
     }
     __syncthreads();   // twiddles
-    butterfly<float, 16>(v);   // v[m1] = sum_k2 X_{k1 + 32 k2} W16^{k2 m1}
-#pragma unroll
-    for (int m1 = 0; m1 < 16; ++m1) tr[p2r_idx(k1 * 16 + m1, p)] = m1 == 0 ? v[0] : cmul(v[m1], tw[k1 * m1]);
-    __syncthreads();
-    // step B: thread (m1 = 2 warp + (c >> 1), j1 = c & 1)
+    line512(v, tw, tr, warp, c, p);
     const int m1 = 2 * warp + (c >> 1), j1 = c & 1;
-#pragma unroll
-    for (int j2 = 0; j2 < 16; ++j2) v[j2] = tr[p2r_idx((j1 + 2 * j2) * 16 + m1, p)];
-    butterfly<float, 16>(v);   // U_j1[n]
     cx<float>* dst = t2 + (size_t)blockIdx.y * t2_stride;
     float mx = 0.f;
 #pragma unroll
     for (int n = 0; n < 16; ++n) {
-        cx<float> u = v[n];
-        if (j1) u = cmul(u, tw[16 * n]);   // W32^n U_1[n]
-        const cx<float> o = {__shfl_xor_sync(0xffffffffu, u.re, 8), __shfl_xor_sync(0xffffffffu, u.im, 8)};
-        // j1 = 0 keeps U_0 + W U_1 (m2 = n), j1 = 1 keeps U_0 - W U_1 (m2 = n + 16)
-        const cx<float> z = j1 ? csub(o, u) : cadd(u, o);
         const int y = m1 + 16 * (n + 16 * j1);
         if (live) {
-            dst[((size_t)x * N + y) * g.nKz + kz] = z;
-            mx = fmaxf(mx, fabsf(z.re) + fabsf(z.im));
+            dst[((size_t)x * N + y) * g.nKz + kz] = v[n];
+            mx = fmaxf(mx, fabsf(v[n].re) + fabsf(v[n].im));
         }
     }
     if (fmax2) {
@@ -710,7 +768,19 @@ cudaError_t launch_n(const FftGeom& g, const cx<float>* delta, const int16_t* sh
     }
     const int nkzb = (g.nKz + C::P - 1) / C::P;
     dim3 g1(g.nK * nkzb, nfields), g2(N * nkzb, nfields), g3(N * ((N + C::P3 - 1) / C::P3), nfields);
-    k_pass1<R, C::P, NN><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);
+    if constexpr (NN == 512 && std::is_same<R, float>::value) {
+        static bool set1r = false;
+        if (!set1r) {
+            if ((e = cudaFuncSetAttribute(k_pass1r, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)p2r_smem_bytes())) != cudaSuccess)
+                return e;
+            set1r = true;
+        }
+        k_pass1r<<<dim3(g.nK * nkzb, nfields), NTHR, p2r_smem_bytes(), st>>>(g, delta, shell_of, radial, d_fields,
+                                                                             tw, t1, t1_stride);
+    } else {
+        k_pass1<R, C::P, NN><<<g1, NTHR, sm12, st>>>(g, delta, shell_of, radial, d_fields, tw, t1, t1_stride);
+    }
     if constexpr (NN == 512 && std::is_same<R, float>::value) {
         static bool set2r = false;
         if (!set2r) {
