@@ -382,8 +382,8 @@ def main():
     elif con_ms >= fft_ms:
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         # DRAM bytes per launch: ncu capture of this kernel at 160^3 with the same bins and
-        # schedule (6.308 GB read + 0.594 GB written per launch) scaled by the points
-        traffic = (6.902e9 * (args.n / 160.0) ** 3
+        # schedule (12.626 GB read + 0.606 GB written per launch) scaled by the points
+        traffic = (13.232e9 * (args.n / 160.0) ** 3
                    if (args.shells, args.prec) == (64, "split_f16") else None)
         ach = flop / (con_ms / 1e3) / 1e12
         roof = {"kernel": "k_contract_tc (tcgen05 split-product contraction)", "bound": "tensor",

@@ -209,13 +209,17 @@ struct TcSched {
 
 // Persistent units: each work gets CTAs in proportion to its cost per
 // K-block, all CTAs together about one per SM; every super-segment of lsup
-// K-blocks is split among the work's CTAs, so all works sweep x at the same
-// pace and share the fields in L2.  The cost of a K-block is set by the
-// pair-product prologue of the tile's 128 pairs and hardly depends on the
-// MMA N (clock traces on GB300: ~1 800 busy cycles per K-block for N = 32
-// and N = 96 alike), so the weight is almost flat in N; weighting by N, as
-// the first versions did, gave works of small N 1.9x the K-blocks per CTA
-// and left the other CTAs waiting at the pacing counter.
+// K-blocks is split among the work's CTAs, so all works sweep x in the same
+// order at about the same rate and read the same fields while they are in
+// L2.  Nothing holds the CTAs together: a global counter that made every CTA
+// wait for the others at each super-segment (any allowed drift, 1 to 16
+// super-segments) cost 6 % at 512^3 against letting them run (224 -> 210 ms),
+// the acquire load on the contended counter sitting in the copy thread's
+// path.  The cost of a K-block is set by the warps' hand-offs and hardly
+// depends on the MMA N (clock traces on GB300: ~1 700 to 1 800 busy cycles per
+// K-block for N = 32 and N = 96 alike), so the weight is almost flat in N;
+// weighting by N, as the first versions did, gave works of small N 1.9x the
+// K-blocks per CTA.
 void assign_units(TcSched& h, size_t npts, int nsm) {
     const int nw = (int)h.works.size();
     const long long nkb = (long long)((npts + 63) / 64);
@@ -1088,7 +1092,7 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
         const int nf = p->nslot() * p->nsh;
         unsigned* fmax2 = p->d_fmax;              // [slot * pad16 + a]  max |T2| per field (bounds |F|)
         CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * ((size_t)p->nslot() * p->pad16 + p->nsh), st));
-        CK(cudaMemsetAsync(p->d_err, 0, 3 * sizeof(int), st));   // error code, pacing counters
+        CK(cudaMemsetAsync(p->d_err, 0, 3 * sizeof(int), st));   // error code
         if ((ms = clear_tail(p, f0, hi, st)) != BSP_OK) return ms;
         const int f16 = p->prec == BSP_SPLIT_F16 ? 1 : 0;
         for (int f0i = 0; f0i < nf; f0i += p->fb32) {
@@ -1108,7 +1112,7 @@ static bsp_status compute_impl(bsp_plan* p, const void* delta_k, double nbar, vo
                                            p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
-                                           p->chunk_kb, partial, p->d_err, (unsigned*)p->d_err + 1, st, p->wait_cycles);
+                                           p->chunk_kb, partial, p->d_err, st, p->wait_cycles);
         if (e != cudaSuccess) return cuda_fail(e, "contract (tensor cores)");
         if ((ms = mark(p, st, 2)) != BSP_OK) return ms;
         const double V = p->box * p->box * p->box;
@@ -1233,7 +1237,7 @@ bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* s
         cx<float>* t2 = (cx<float>*)(base + L.t2);
         unsigned* fmax2 = p->d_fmax;                    // [slot * pad16 + a] max |T2| per field (bounds |F|)
         CK(cudaMemsetAsync(p->d_fmax, 0, sizeof(unsigned) * ((size_t)p->nslot() * p->pad16 + 2 * nf), st));
-        CK(cudaMemsetAsync(p->d_err, 0, 3 * sizeof(int), st));   // error code, pacing counters
+        CK(cudaMemsetAsync(p->d_err, 0, 3 * sizeof(int), st));   // error code
         if ((ms = clear_tail(p, f0, hi, st)) != BSP_OK) return ms;
         const int f16 = p->prec == BSP_SPLIT_F16 ? 1 : 0;
         for (int fi = 0; fi < nfields; fi += p->fb32) {
@@ -1254,7 +1258,7 @@ bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* s
                                            p->d_tc_works, p->d_tc_units,
                                            (int)p->tc_sched.units.size(), p->tc_sched.lsup, p->tc_sched.nsup,
                                            p->d_tc_pairs, 0, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
-                                           p->chunk_kb, part, p->d_err, (unsigned*)p->d_err + 1, st, p->wait_cycles);
+                                           p->chunk_kb, part, p->d_err, st, p->wait_cycles);
         if (e != cudaSuccess) return cuda_fail(e, "contract (modal, tensor cores)");
         ++launches;
         if (p->need_u) {
@@ -1262,7 +1266,7 @@ bsp_status bsp_modal_compute(bsp_plan* p, const void* delta_k, void* ws, void* s
                                    p->d_tcu_works, p->d_tcu_units,
                                    (int)p->tc_u_sched.units.size(), p->tc_u_sched.lsup, p->tc_u_sched.nsup,
                                    p->d_tcu_pairs, p->slot2 * p->pad16, fmax2, 2.f * (float)p->geom.nKz, p->nprod,
-                                   p->chunk_kb, upart, p->d_err, (unsigned*)p->d_err + 2, st, p->wait_cycles);
+                                   p->chunk_kb, upart, p->d_err, st, p->wait_cycles);
             if (e != cudaSuccess) return cuda_fail(e, "contract (modal U, tensor cores)");
             ++launches;
         }

@@ -150,7 +150,7 @@ cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_ro
                                int groups, long long nkb, const TcWork* works, const TcUnit* units, int nunits,
                                int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
-                               unsigned* pace, cudaStream_t st, long long wait_cycles = 0);
+                               cudaStream_t st, long long wait_cycles = 0);
 
 // ---- density input stage (bsp_fft.cu) ----
 struct DensityLayout {   // byte offsets in the caller's workspace

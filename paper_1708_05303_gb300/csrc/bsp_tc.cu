@@ -292,18 +292,6 @@ __device__ __forceinline__ double f32_ldexp_f64(float f, int k) {
     return __longlong_as_double((long long)b);
 }
 
-// Wait until *ctr >= target (acquire); false after ~4 s.
-__device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target, long long limit) {
-    const long long t0 = clock64();
-    while (true) {
-        unsigned v;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
-        if (v >= target) return true;
-        if (clock64() - t0 > limit) return false;
-        __nanosleep(64);
-    }
-}
-
 __device__ __forceinline__ void set_abort(TcSmem& S, int* err, int code) {
     S.abort = 1;
     atomicOr(err, code);
@@ -316,7 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   const int2* __restrict__ pair_shells, int pair_base,
                   const unsigned* __restrict__ fmax2, float bound_mul, const TcUnit* __restrict__ units,
                   int lsup, int nsup, int nprod, int CHUNK, double* __restrict__ partial,
-                  int* __restrict__ err, unsigned* __restrict__ pace, int drift, long long wlim) {
+                  int* __restrict__ err, long long wlim) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -411,13 +399,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 const int sup = k / unit.len, kin = k % unit.len;
-                // pacing: super-segment sup starts once every CTA has issued the loads
-                // of super-segments < sup - drift, so that works whose K-blocks cost
-                // different times still read the same fields while they sit in L2
-                if (pace && kin == 0 && sup > drift && !wait_count(pace, (unsigned)(gridDim.x * (sup - drift)), wlim)) {
-                    set_abort(S, err, 128);
-                    break;
-                }
                 const long long kb = (long long)sup * lsup + unit.start + kin;
                 if (kb < nkb_real) {
                     mbar_expect_tx(&S.tma_full[s], bytes);
@@ -431,7 +412,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mbar_expect_tx(&S.tma_full[s], 0);   // past the grid: nothing to load
                 }
                 issued = k + 1;
-                if (pace && kin == unit.len - 1) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(pace) : "memory");
             }
             // copies in flight must land before the CTA can exit: the last use of each
             // stage (always the long limit, whatever the pipeline waits use)
@@ -640,11 +620,10 @@ cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_ro
                                int groups, long long nkb, const TcWork* works, const TcUnit* units, int nunits,
                                int lsup, int nsup, const int2* pair_shells, int pair_base, const unsigned* fmax2,
                                float bound_mul, int nprod, int chunk_kb, double* partial, int* err,
-                               unsigned* pace, cudaStream_t st, long long wait_cycles) {
+                               cudaStream_t st, long long wait_cycles) {
     const size_t smem = tc_smem_bytes();
     const long long wlim = wait_cycles > 0 ? wait_cycles : WAIT_CYCLES;
     static bool set16 = false, setb = false;   // once per kernel, never inside a graph capture
-    static int resident = -1;                  // CTAs that fit on the device at once
     auto kern = f16 ? k_contract_tc<true> : k_contract_tc<false>;
     cudaError_t e;
     bool& set = f16 ? set16 : setb;
@@ -653,30 +632,13 @@ cudaError_t launch_contract_tc(bool f16, const float* f0, int f0_rows, int f0_ro
             return e;
         set = true;
     }
-    if (resident < 0) {
-        int dev = 0, nsm = 0, per = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-            (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TC_THREADS, smem)) != cudaSuccess)
-            return e;
-        resident = nsm * per;
-    }
-    // pacing needs every CTA resident at once: a cooperative launch guarantees it
-    const bool paced = pace != nullptr && nunits <= resident;
-    const int drift = 2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nunits);
     cfg.blockDim = dim3(TC_THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = paced ? 1 : 0;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    unsigned* pc = paced ? pace : nullptr;
     return cudaLaunchKernelEx(&cfg, kern, f0, f0_rows, f0_row0, planes, groups, nkb, works, pair_shells, pair_base, fmax2, bound_mul, units, lsup, nsup,
-                              nprod, chunk_kb, partial, err, pc, drift, wlim);
+                              nprod, chunk_kb, partial, err, wlim);
 }
 
 }  // namespace bsp
