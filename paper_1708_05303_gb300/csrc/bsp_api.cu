@@ -219,7 +219,12 @@ struct TcSched {
 // depends on the MMA N (clock traces on GB300: ~1 700 to 1 800 busy cycles per
 // K-block for N = 32 and N = 96 alike), so the weight is almost flat in N;
 // weighting by N, as the first versions did, gave works of small N 1.9x the
-// K-blocks per CTA.
+// K-blocks per CTA.  With whole CTAs per work the split is uneven when the
+// works do not divide the SMs (17 works on 152 SMs at 512^3: one work of 8
+// CTAs, whose CTAs run 12.5 % longer).  Equal shares with a CTA running the
+// tail of one work and then the head of the next were slower (205 -> 219 ms):
+// the second unit starts where the other CTAs of its work passed long ago
+// and reads its fields from DRAM instead of L2.
 void assign_units(TcSched& h, size_t npts, int nsm) {
     const int nw = (int)h.works.size();
     const long long nkb = (long long)((npts + 63) / 64);
