@@ -489,10 +489,38 @@ __global__ void __launch_bounds__(NTHR) k_pass2r(FftGeom g, const cx<float>* __r
     }
 }
 
+// Staging layouts of pass 3's z-lines in shared memory (element m of line p
+// = F[2m] + i F[2m+1]).  Stockham passes: the i/8-padded index-fast layout.
+template <int P>
+struct StageStockham {
+    __device__ static int idx(int p, int m, int M) { return sidx<false, P>(p, m, M); }
+    template <typename R>
+    __device__ static void load4(const cx<R>* res, int p, int m0, int M, cx<R> (&v)[4]) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = res[idx(p, m0 + i, M)];
+    }
+};
+// Register pass 3 (M = 256): 16-element groups padded by 2 elements, lines
+// 288 elements apart, so the 4 elements of a 16-byte output chunk are two
+// aligned 16-byte loads and a quarter warp's loads fall on distinct banks.
+struct Stage3r {
+    static constexpr int PS = 288;
+    __device__ static int idx(int p, int m, int) { return p * PS + m + (m >> 4) * 2; }
+    template <typename R>
+    __device__ static void load4(const cx<R>* res, int p, int m0, int, cx<R> (&v)[4]) {
+        const float4* q = reinterpret_cast<const float4*>(res + idx(p, m0, 0));
+        const float4 a = q[0], b = q[1];
+        v[0] = {a.x, a.y};
+        v[1] = {a.z, a.w};
+        v[2] = {b.x, b.y};
+        v[3] = {b.z, b.w};
+    }
+};
+
 // Output of pass 3 for P consecutive y of one x: the real values of each
 // z-line, res[sidx<false, P>(p, m, M)] = F[2m] + i F[2m+1], scaled and
 // written as the field's FP32 row and/or 16-bit hi/lo planes.
-template <typename R, int P>
+template <typename R, int P, class Stage = StageStockham<P>>
 __device__ __forceinline__ void pass3_store(const FftGeom& g, int N, int M, int x, int y0, const cx<R>* res,
                                             const FieldDesc& fd, R* __restrict__ out, size_t out_stride,
                                             uint32_t* __restrict__ hi, uint32_t* __restrict__ lo, int f16,
@@ -532,8 +560,7 @@ __device__ __forceinline__ void pass3_store(const FftGeom& g, int N, int M, int 
                 const size_t kb = pos >> 5;
                 const int w = (int)(pos & 31);   // a multiple of 4
                 cx<R> v[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = res[sidx<false, P>(p, m0 + i, M)];
+                Stage::load4(res, p, m0, M, v);
                 if (dst) {
                     cx<R>* row = reinterpret_cast<cx<R>*>(dst) + (kb * (size_t)lay.rows32 + (size_t)fd.out32) * 32;
                     const int J = w >> 1;   // 16-byte chunks J, J + 1 of the 256-byte FP32 row
@@ -589,7 +616,7 @@ __device__ __forceinline__ void pass3_store(const FftGeom& g, int N, int M, int 
             p32 = (kb * (size_t)lay.rows32 + (size_t)fd.out32) * 32 + (size_t)(((J & 8) | ((J & 7) ^ r32)) * 2 + (w & 1));
             p16 = kb * (size_t)lay.groups16 * 512 + (size_t)((((w >> 2) ^ r16) << 2) | (w & 3));
         }
-        const cx<R> v = res[sidx<false, P>(p, m, M)];
+        const cx<R> v = res[Stage::idx(p, m, M)];
         if (dst) {
             reinterpret_cast<cx<R>*>(dst)[p32] = cx<R>{v.re * s7, v.im * s7};
             if (f0max) mx = fmaxf(mx, fmaxf(fabsf((float)v.re), fabsf((float)v.im)));
@@ -674,10 +701,9 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
 // instead of one per Stockham stage, and every thread busy in both DFTs.
 constexpr int P3R = 16;
 constexpr int P3R_TS = 16 * 17;   // transpose rows per line: 16 rows of 16 + 1 pad
-constexpr size_t p3r_smem_bytes() {
-    return sizeof(cx<float>) * (512 + (size_t)smem_elems<false, P3R>(256));
-}
-static_assert(P3R * P3R_TS <= smem_elems<false, P3R>(256), "transpose fits in the output buffer");
+constexpr int P3R_BUF = P3R * Stage3r::PS;   // staging buffer (the transpose fits in it)
+constexpr size_t p3r_smem_bytes() { return sizeof(cx<float>) * (512 + 256 + (size_t)P3R_BUF); }
+static_assert(P3R * P3R_TS <= P3R_BUF, "transpose fits in the output buffer");
 
 __global__ void __launch_bounds__(NTHR) k_pass3r(FftGeom g, const cx<float>* __restrict__ t2, size_t t2_stride,
                                                  const cx<float>* __restrict__ twg,
@@ -689,10 +715,12 @@ __global__ void __launch_bounds__(NTHR) k_pass3r(FftGeom g, const cx<float>* __r
     constexpr int N = 512, M = 256;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
-    cx<float>* buf = tw + N;
+    cx<float>* tw2 = tw + N;     // [m1][t] = W256^{t m1}: conflict-free reads across t
+    cx<float>* buf = tw2 + 256;
     const int x = blockIdx.x / (N / P3R), y0 = (blockIdx.x % (N / P3R)) * P3R;
     const int p = threadIdx.x >> 4, t = threadIdx.x & 15;
     for (int i = threadIdx.x; i < N; i += NTHR) tw[i] = twg[i];
+    tw2[threadIdx.x] = twg[(2 * (threadIdx.x & 15) * (threadIdx.x >> 4)) & (N - 1)];
     __syncthreads();
     const int nKz = g.nKz;
     const cx<float>* h = t2 + (size_t)blockIdx.y * t2_stride + ((size_t)x * N + y0 + p) * nKz;
@@ -711,17 +739,17 @@ __global__ void __launch_bounds__(NTHR) k_pass3r(FftGeom g, const cx<float>* __r
     butterfly<float, 16>(v);   // v[m1] = sum_k2 Z_{t + 16 k2} W16^{k2 m1}
     cx<float>* tr = buf + p * P3R_TS;
 #pragma unroll
-    for (int m1 = 0; m1 < 16; ++m1) tr[m1 * 17 + t] = m1 == 0 ? v[0] : cmul(v[m1], tw[2 * t * m1]);   // W256^{t m1}
+    for (int m1 = 0; m1 < 16; ++m1) tr[m1 * 17 + t] = m1 == 0 ? v[0] : cmul(v[m1], tw2[m1 * 16 + t]);   // W256^{t m1}
     __syncthreads();
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) v[k1] = tr[t * 17 + k1];
     butterfly<float, 16>(v);   // v[m2] = z_{t + 16 m2}
     __syncthreads();           // every line's transpose is read before the output layout reuses it
 #pragma unroll
-    for (int m2 = 0; m2 < 16; ++m2) buf[sidx<false, P3R>(p, t + 16 * m2, M)] = v[m2];
+    for (int m2 = 0; m2 < 16; ++m2) buf[Stage3r::idx(p, t + 16 * m2, M)] = v[m2];
     __syncthreads();
-    pass3_store<float, P3R>(g, N, M, x, y0, buf, fields[blockIdx.y], out, out_stride, hi, lo, f16, fmax2, f0max,
-                            lay);
+    pass3_store<float, P3R, Stage3r>(g, N, M, x, y0, buf, fields[blockIdx.y], out, out_stride, hi, lo, f16, fmax2,
+                                     f0max, lay);
 }
 
 template <typename R>
