@@ -467,8 +467,8 @@ bsp_status bsp_phase_times(bsp_plan* plan, double* ms, int* ncalls, int* launche
  * call's contents; nothing in them needs to start at zero (each partial is
  * written before it is read), but calls that overlap on the GPU (different
  * streams, or host threads) race on them.  The first call on each device
- * looks up the arrays' device addresses (cudaGetSymbolAddress, synchronous);
- * make that first call before any stream capture begins.
+ * looks up the arrays' device addresses with cudaGetSymbolAddress, which
+ * synchronises with the device.
  *
  * The triplet list is copied with cudaMemcpyAsync on `stream`.  From
  * pageable host memory the call returns once the copy has been staged; from
