@@ -644,6 +644,12 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
         }
     for (int n2 = 0; n2 <= g.n2max; ++n2)
         if (shell_of[n2] >= 0) p->n2top = n2;
+    // per shell: the largest |frequency component| of its modes, floor(sqrt(max |n|^2))
+    std::vector<int> kext(n_shells, 1);
+    for (int n2 = 0, f = 0; n2 <= g.n2max; ++n2) {
+        while ((long long)(f + 1) * (f + 1) <= n2) ++f;
+        if (shell_of[n2] >= 0) kext[shell_of[n2]] = std::min(std::max(kext[shell_of[n2]], f), g.K);
+    }
     std::vector<cx<double>> tw64(n);
     std::vector<cx<float>> tw32(n);
     for (int t = 0; t < n; ++t) {
@@ -659,8 +665,8 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
     for (int s = 0; s < p->nslot(); ++s)
         for (int a = 0; a < n_shells; ++a) {
             const int f = s * n_shells + a;
-            fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, f, -1, {0, 0, 0}});
-            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, s == 0 ? a : -1, s * pad16 + a, {0, 0, 0}});
+            fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, f, -1, kext[a], {0, 0}});
+            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_DELTA, s == 0 ? a : -1, s * pad16 + a, kext[a], {0, 0}});
         }
     if (p->shot) {
         // S^l_a = w_l |delta|^2 on a, then W^l_a = w_l on a (W^0 = the unit fields I)
@@ -669,14 +675,14 @@ bsp_status bsp_plan_create(bsp_plan** out, int n, double box, int n_shells, cons
             for (int s = 0; s < p->nslot(); ++s)
                 for (int a = 0; a < n_shells; ++a)
                     fdd.push_back(FieldDesc{a, p->slot_ell[s], kind == 0 ? FIELD_POWER : FIELD_UNIT,
-                                            (kind + 1) * nfs + s * n_shells + a, -1, {0, 0, 0}});
+                                            (kind + 1) * nfs + s * n_shells + a, -1, kext[a], {0, 0}});
     }
-    for (int a = 0; a < n_shells; ++a) fdu.push_back(FieldDesc{a, 0, FIELD_UNIT, a, -1, {0, 0, 0}});
+    for (int a = 0; a < n_shells; ++a) fdu.push_back(FieldDesc{a, 0, FIELD_UNIT, a, -1, kext[a], {0, 0}});
     bsp_status st;
     if ((st = upload(&p->d_shell_of, shell_of)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||
         (st = upload(&p->d_tw64, tw64)) != BSP_OK || (st = upload(&p->d_fd_delta, fdd)) != BSP_OK ||
         (st = upload(&p->d_fd_unit, fdu)) != BSP_OK || (st = upload(&p->d_fd_tc, fdt)) != BSP_OK ||
-        (st = upload(&p->d_fd_raw, std::vector<FieldDesc>{FieldDesc{0, 0, FIELD_RAW, 0, -1, {0, 0, 0}}})) != BSP_OK ||
+        (st = upload(&p->d_fd_raw, std::vector<FieldDesc>{FieldDesc{0, 0, FIELD_RAW, 0, -1, 0, {0, 0}}})) != BSP_OK ||
         (st = upload(&p->d_err, std::vector<int>{0, 0, 0})) != BSP_OK ||
         (st = upload(&p->d_fmax, std::vector<unsigned>((size_t)p->nslot() * pad16 + n_shells, 0u))) != BSP_OK) {
         delete p;
@@ -826,11 +832,11 @@ bsp_status bsp_plan_create_modal(bsp_plan** out, int n, double box, int n_funcs,
     for (int s = 0; s < p->nslot(); ++s)
         for (int a = 0; a < nf; ++a) {
             const int f = s * nf + a;
-            fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_RADIAL, f, -1, {0, 0, 0}});
+            fdd.push_back(FieldDesc{a, p->slot_ell[s], FIELD_RADIAL, f, -1, 0, {0, 0}});
             int o32 = -1;
             if (s == 0) o32 = a;
             else if (p->need_u && s == p->slot2) o32 = nf + a;
-            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_RADIAL, o32, s * p->pad16 + a, {0, 0, 0}});
+            fdt.push_back(FieldDesc{a, p->slot_ell[s], FIELD_RADIAL, o32, s * p->pad16 + a, 0, {0, 0}});
         }
     bsp_status st;
     if ((st = upload(&p->d_radial, tab)) != BSP_OK || (st = upload(&p->d_tw32, tw32)) != BSP_OK ||

@@ -220,6 +220,14 @@ __device__ __forceinline__ cx<R>* fft_ct(cx<R>* a, cx<R>* b, const cx<R>* tw, in
 
 __device__ __forceinline__ int freq_of(int idx, int n) { return idx < n / 2 ? idx : idx - n; }
 
+// Largest |frequency component| where the field can be nonzero (its shell's
+// outer edge, at most K).  Every pass uses the same bound: pass 1 skips the
+// pencils beyond it (f_y or f_z), pass 2 skips the f_z beyond it and reads no
+// f_y beyond it, pass 3 reads no f_z beyond it, so nothing unwritten is read.
+__device__ __forceinline__ int field_ext(const FieldDesc& fd, const FftGeom& g) {
+    return fd.kext > 0 ? min(fd.kext, g.K) : g.K;
+}
+
 // W_f(n): the field's radial factor times w_l(mu), mu^2 = n_z^2/|n|^2.
 template <typename R>
 __device__ __forceinline__ R filter_weight(const FieldDesc& fd, int n2, int fz, const int16_t* shell_of,
@@ -290,6 +298,8 @@ __global__ void __launch_bounds__(NTHR) k_pass1(FftGeom g, const cx<float>* __re
     const int cy = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P;
     const int fy = g.pruned ? cy - g.K : freq_of(cy, N);
     const int iy = (fy + N) % N;
+    const int ke = field_ext(fd, g);
+    if (fy > ke || fy < -ke || kz0 > ke) return;   // zero there, and pass 2 reads none of it
     for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
     for (int e = threadIdx.x; e < N * P; e += NTHR) {
         const int p = e % P, ix = e / P, kz = kz0 + p;
@@ -336,13 +346,15 @@ __global__ void __launch_bounds__(NTHR) k_pass2(FftGeom g, const cx<R>* __restri
     cx<R>* scr = buf + smem_elems<true, P>(N);
     const int nkzb = (g.nKz + P - 1) / P;
     const int x = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P;
+    const int ke = field_ext(fields[blockIdx.y], g);
+    if (kz0 > ke) return;   // zero there, and pass 3 reads none of it
     const cx<R>* src = t1 + (size_t)blockIdx.y * t1_stride;
     for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
     for (int e = threadIdx.x; e < N * P; e += NTHR) {
         const int p = e % P, iy = e / P, kz = kz0 + p;
         const int fy = freq_of(iy, N);
         cx<R> val = {(R)0, (R)0};
-        if (kz < g.nKz && (!g.pruned || (fy >= -g.K && fy <= g.K))) {
+        if (kz < g.nKz && fy >= -ke && fy <= ke) {
             const int cy = g.pruned ? fy + g.K : iy;
             val = src[((size_t)cy * N + x) * g.nKz + kz];
         }
@@ -423,6 +435,8 @@ __global__ void __launch_bounds__(NTHR) k_pass1r(FftGeom g, const cx<float>* __r
     const int cy = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P2R;
     const int fy = g.pruned ? cy - g.K : freq_of(cy, N);
     const int iy = (fy + N) % N;
+    const int ke = field_ext(fd, g);
+    if (fy > ke || fy < -ke || kz0 > ke) return;   // zero there, and pass 2 reads none of it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = lane & 7, c = lane >> 3;
     const int kz = kz0 + p;
@@ -451,6 +465,8 @@ __global__ void __launch_bounds__(NTHR) k_pass2r(FftGeom g, const cx<float>* __r
     cx<float>* tr = tw + N;
     const int nkzb = (g.nKz + P2R - 1) / P2R;
     const int x = blockIdx.x / nkzb, kz0 = (blockIdx.x % nkzb) * P2R;
+    const int ke = field_ext(fields[blockIdx.y], g);
+    if (kz0 > ke) return;   // zero there, and pass 3 reads none of it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = lane & 7, c = lane >> 3;   // line (f_z offset) and lane group
     const int kz = kz0 + p;
@@ -464,7 +480,7 @@ __global__ void __launch_bounds__(NTHR) k_pass2r(FftGeom g, const cx<float>* __r
     for (int k2 = 0; k2 < 16; ++k2) {
         const int iy = k1 + 32 * k2, fy = iy < N / 2 ? iy : iy - N;
         cx<float> val = {0.f, 0.f};
-        if (live && (!g.pruned || (fy >= -g.K && fy <= g.K))) {
+        if (live && fy >= -ke && fy <= ke) {
             const int cy = g.pruned ? fy + g.K : iy;
             val = src[((size_t)cy * N + x) * g.nKz + kz];
         }
@@ -666,6 +682,7 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
     const int nyb = (N + P - 1) / P;
     const int x = blockIdx.x / nyb, y0 = (blockIdx.x % nyb) * P;
     const cx<R>* src = t2 + (size_t)blockIdx.y * t2_stride;
+    const int nk = field_ext(fields[blockIdx.y], g) + 1;   // f_z read: 0 .. nk - 1
     for (int t = threadIdx.x; t < N; t += NTHR) tw[t] = twg[t];
     __syncthreads();
     for (int e = threadIdx.x; e < M * P; e += NTHR) {
@@ -674,8 +691,8 @@ __global__ void __launch_bounds__(NTHR) k_pass3(FftGeom g, const cx<R>* __restri
         if (y < N) {
             const cx<R>* h = src + ((size_t)x * N + y) * g.nKz;
             cx<R> a = {(R)0, (R)0}, b = {(R)0, (R)0};
-            if (k < g.nKz) a = h[k];
-            if (M - k < g.nKz) b = h[M - k];
+            if (k < nk) a = h[k];
+            if (M - k < nk) b = h[M - k];
             if (k == 0) { a.im = (R)0; b.im = (R)0; }   // H_0 and H_M: real parts only
             const cx<R> bc = {b.re, -b.im};
             const cx<R> s = cadd(a, bc), d = csub(a, bc);
@@ -723,14 +740,15 @@ __global__ void __launch_bounds__(NTHR) k_pass3r(FftGeom g, const cx<float>* __r
     tw2[threadIdx.x] = twg[(2 * (threadIdx.x & 15) * (threadIdx.x >> 4)) & (N - 1)];
     __syncthreads();
     const int nKz = g.nKz;
+    const int nk = field_ext(fields[blockIdx.y], g) + 1;   // f_z read: 0 .. nk - 1
     const cx<float>* h = t2 + (size_t)blockIdx.y * t2_stride + ((size_t)x * N + y0 + p) * nKz;
     cx<float> v[16];
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) {
         const int k = t + 16 * k2;
         cx<float> a = {0.f, 0.f}, b = {0.f, 0.f};
-        if (k < nKz) a = h[k];
-        if (M - k < nKz) b = h[M - k];
+        if (k < nk) a = h[k];
+        if (M - k < nk) b = h[M - k];
         if (k == 0) { a.im = 0.f; b.im = 0.f; }   // H_0 and H_M: real parts only
         const cx<float> bc = {b.re, -b.im};
         const cx<float> s = cadd(a, bc), d = csub(a, bc);

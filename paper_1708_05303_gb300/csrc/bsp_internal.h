@@ -34,7 +34,11 @@ struct FieldDesc {
     int kind;    // FieldKind
     int out32;   // index of the FP32/FP64 output field, or -1
     int out16;   // index of the 16-bit hi/lo output planes, or -1
-    int pad[3];
+    // the field's spectrum vanishes where any |frequency component| > kext
+    // (its shell's outer edge); <= 0: the plan's extent K.  Pass 1 skips the
+    // pencils beyond it and passes 2 and 3 read nothing beyond it.
+    int kext;
+    int pad[2];
 };
 
 // Geometry of the pruned inverse FFT.  Only frequencies |f| <= K per axis
