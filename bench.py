@@ -381,10 +381,11 @@ def main():
                 "issued_frac": (issued / (con_ms / 1e3) / 1e12) / peak}
     elif con_ms >= fft_ms:
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        # DRAM bytes per launch: ncu capture of this kernel at 160^3 with the same bins and
-        # schedule (12.626 GB read + 0.606 GB written per launch) scaled by the points
-        traffic = (13.232e9 * (args.n / 160.0) ** 3
-                   if (args.shells, args.prec) == (64, "split_f16") else None)
+        # DRAM bytes per launch: ncu capture of this kernel at 160^3 with the same bins,
+        # schedule and default 64-point chunk (11.385 GB read + 0.597 GB written per
+        # launch) scaled by the points
+        traffic = (11.982e9 * (args.n / 160.0) ** 3
+                   if (args.shells, args.prec, args.chunk) == (64, "split_f16", 0) else None)
         ach = flop / (con_ms / 1e3) / 1e12
         roof = {"kernel": "k_contract_tc (tcgen05 split-product contraction)", "bound": "tensor",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,

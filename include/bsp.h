@@ -171,8 +171,8 @@ bsp_status bsp_modal_project(int n_keep, const double* gamma, int n_rhs, const d
  *   on the valid bins: rows would not line up); with autotune != 0 times,
  *   per size, the FFT batch {4, 16, 64} against the CUDA-core contraction
  *   grid {1024, 2048, 4096} (BSP_FP32) or the tensor-core tile height
- *   {96, 64} x accumulation chunk {256, 128} points (bsp_plan_tune_tc;
- *   never a chunk longer than the default) and keeps the fastest; then
+ *   {96, 64} at the default 64-point accumulation chunk (bsp_plan_tune_tc;
+ *   longer chunks are less accurate) and keeps the fastest; then
  *   captures bsp_compute into one CUDA graph per (size, input buffer).
  *   Synchronises `stream`.
  * bsp_batch_info / bsp_batch_tuning / bsp_batch_bins: n_bins, the
@@ -402,16 +402,19 @@ bsp_status bsp_plan_tune_tc(bsp_plan* plan, int max_rows, int chunk_points);
 
 /*
  * Tensor-core paths only: the number of x-points (a multiple of 64, 64 ..
- * 2^20; default 256) summed in an FP32 tensor-memory accumulator before it
- * is folded into the compensated running sums.  Shorter chunks are more
- * accurate and cost more epilogue work.
+ * 2^20; default 64) summed in an FP32 tensor-memory accumulator before it
+ * is added to the FP32 running sum (itself added to FP64 every 8192 points).
+ * Every MMA truncates each of its addends to 25 bits below the largest one,
+ * so a longer chunk (a larger accumulator) loses more of every product;
+ * shorter chunks are more accurate until the running sum's own rounding
+ * dominates, and cost more epilogue work.
  */
 bsp_status bsp_set_accumulation_chunk(bsp_plan* plan, int points);
 
 /*
  * Tensor-core paths only: the limit, in SM clock cycles, of every wait
  * inside the contraction's pipeline (copies landed, products written, MMAs
- * done, accumulator drained, the pacing counter); 0 restores the default
+ * done, accumulator drained); 0 restores the default
  * (2^33 cycles, about 4 s).  A wait that runs out makes the kernel record
  * the error in the plan's error word (bsp_device_status), stop issuing work,
  * wait for its own copies and MMAs in flight (always with the default limit)

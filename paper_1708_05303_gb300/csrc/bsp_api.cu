@@ -426,7 +426,7 @@ struct bsp_plan {
     BinLoc* d_tc_loc = nullptr;
     int* d_err = nullptr;
     unsigned* d_fmax = nullptr;   // per-field magnitude bounds for the 16-bit scaling
-    int chunk_kb = 4;             // K-blocks (64 points each) per FP32 tensor-memory accumulation
+    int chunk_kb = 1;             // K-blocks (64 points each) per FP32 tensor-memory accumulation
     long long wait_cycles = 0;    // tensor-core pipeline wait limit in clock cycles (0: the kernel's default)
     int tc_max_boxes = 12;        // tensor-core works: at most this many boxes of 8 field rows (N <= 8 x this)
     size_t f0_bytes = 0, plane_bytes = 0, tc_part_bytes = 0;
@@ -1341,7 +1341,8 @@ bsp_status bsp_plan_stats(const bsp_plan* p, double* st) {
         works = (double)p->tc_sched.works.size();
         nsplit = (double)p->tc_sched.units.size();
     } else {
-        issued = (double)p->comp_sched.works.size() * 64.0 * 64.0;
+        // 64 pairs times the 16-row blocks that hold rows (k_contract_cc32 skips the rest)
+        for (const Work& w : p->comp_sched.works) issued += 64.0 * 16.0 * ((w.nrows + 15) / 16);
         works = (double)p->comp_sched.works.size();
         nsplit = p->comp_sched.nsplit;
     }

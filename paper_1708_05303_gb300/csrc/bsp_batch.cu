@@ -171,8 +171,9 @@ bsp_status bsp_batch_prepare(bsp_batch* bt, void* ws, void* stream, int autotune
     if (cudaMemsetAsync(in_buf(bt, ws, 0), 0, 2 * r256(bt->in_max), st) != cudaSuccess) return BSP_ECUDA;
     // autotune, timed on the (zero) input: the FFT batch width, and the
     // contraction grid target (CUDA-core plans) or the tensor-core tile height
-    // and accumulation chunk (no chunk longer than the default 256 points, so
-    // the tuned schedule is never less accurate than the untuned one)
+    // (tensor-core plans; the accumulation chunk stays at the library's default
+    // of 64 points, the shortest: the tensor core's truncating FP32
+    // accumulation loses more on longer chunks, so tuning never trades accuracy)
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BSP_ECUDA;
     const bool tc = bt->prec != BSP_FP32;
@@ -181,16 +182,15 @@ bsp_status bsp_batch_prepare(bsp_batch* bt, void* ws, void* stream, int autotune
         double best = 1e30;
         const int ctas[] = {1024, 2048, 4096};
         const int rows_opt[] = {96, 64};
-        const int chunk_opt[] = {256, 128};
         const int fbs[] = {4, 16, 64};
-        const int na = autotune ? (tc ? 4 : 3) : 1;
+        const int na = autotune ? (tc ? 2 : 3) : 1;
         for (int ai = 0; ai < na; ++ai)
             for (int fi = 0; fi < (autotune ? 3 : 1); ++fi) {
                 const int f = autotune ? fbs[fi] : 0;
                 int c = 0, rw = 0, ck = 0;
                 if (autotune && tc) {
-                    rw = rows_opt[ai / 2];
-                    ck = chunk_opt[ai % 2];
+                    rw = rows_opt[ai];
+                    ck = 64;
                     if (bsp_plan_tune_tc(bt->plans[s], rw, ck) != BSP_OK) continue;
                 } else if (autotune) {
                     c = ctas[ai];

@@ -174,9 +174,9 @@ __global__ void __launch_bounds__(CC_THREADS) k_contract_cc(const R* __restrict_
 // two stages in flight): rows A_r and pair factors X_s (and Y_s) for 32
 // points land in shared memory in their natural [field][x] layout while the
 // previous 32 points are multiplied.  Thread (ty, tx) owns rows ty + 16 i and
-// pairs 4 tx + j (i, j < 4): per 4 points it reads 4 float4 of A (8 distinct
+// pairs 4 tx + j (i < NI, j < 4): per 4 points it reads NI float4 of A (8 distinct
 // rows per warp: conflict-free with the 36-float row stride) and 4 float4 of
-// the pair products P[x][p], then does 64 FMAs.  Block sums of 64 points are
+// the pair products P[x][p], then does 16 NI FMAs.  Block sums of 64 points are
 // folded into compensated (TwoSum) pairs, as in k_contract_cc.
 constexpr int C2_XS = 32;                 // points per stage
 constexpr int C2_LD = C2_XS + 4;          // row stride (floats) of the staged fields
@@ -200,40 +200,27 @@ struct Cc2Smem {
     int rf[CC_ROWS];
 };
 
-template <bool TWO, bool SYM>
-__global__ void __launch_bounds__(CC_THREADS, 2) k_contract_cc32(const float* __restrict__ rows,
-                                                                 const float* __restrict__ px,
-                                                                 const float* __restrict__ py, size_t fstride,
-                                                                 const Work* __restrict__ works,
-                                                                 const int2* __restrict__ pair_fields,
-                                                                 const int* __restrict__ row_fields, size_t npts,
-                                                                 size_t seg, double* __restrict__ partial) {
-    extern __shared__ __align__(16) unsigned char c2_raw[];
-    Cc2Smem& S = *reinterpret_cast<Cc2Smem*>(c2_raw);
-    const Work w = works[blockIdx.x];
+// Body of the FP32 contraction for a work of at most 16 NI rows: rows fill
+// from 0 and thread (ty, tx) owns rows ty + 16 i, so the row blocks i >= NI
+// are empty and neither staged nor multiplied (the tiles' a-ranges give
+// works of 3 x (a-range) rows, most far below 64).
+template <bool TWO, bool SYM, int NI>
+__device__ __forceinline__ void cc32_body(Cc2Smem& S, const Work& w, const float* __restrict__ rows,
+                                          const float* __restrict__ px, const float* __restrict__ py,
+                                          size_t fstride, size_t npts, size_t seg, double* __restrict__ partial) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ty = (warp & 1) * 8 + (lane >> 2);     // rows ty + 16 i
     const int tx = (warp >> 1) * 4 + (lane & 3);     // pairs 4 tx + j
-    for (int i = tid; i < CC_COLS; i += CC_THREADS) {
-        int2 v = {-1, -1};
-        if (i < w.npairs) {
-            v = pair_fields[w.pair0 + i];
-            v.x -= w.shell_lo;
-            v.y -= w.shell_lo;
-        }
-        S.pf[i] = v;
-    }
-    for (int i = tid; i < CC_ROWS; i += CC_THREADS) S.rf[i] = i < w.nrows ? row_fields[w.rowbase + i] : -1;
-    __syncthreads();
     const size_t x_begin = (size_t)blockIdx.y * seg;
     const size_t x_end = min(npts, x_begin + seg);
     const int nst = x_end > x_begin ? (int)((x_end - x_begin + C2_XS - 1) / C2_XS) : 0;
     const int nsh = w.nshell;
+    constexpr int NR = 16 * NI;   // staged rows
 
     // stage s -> buffer b: 8 chunks of 4 floats per field row, zero-filled past x_end
     auto load = [&](int st, int b) {
         const size_t x0 = x_begin + (size_t)st * C2_XS;
-        const int nrow_all = CC_ROWS + nsh * (TWO ? 2 : 1);
+        const int nrow_all = NR + nsh * (TWO ? 2 : 1);
         for (int e = tid; e < nrow_all * 8; e += CC_THREADS) {
             const int r = e >> 3, ch = e & 7;
             const size_t x = x0 + 4 * ch;
@@ -241,17 +228,17 @@ __global__ void __launch_bounds__(CC_THREADS, 2) k_contract_cc32(const float* __
             const float* src;
             float* dst;
             int bytes = rem * 4;
-            if (r < CC_ROWS) {
+            if (r < NR) {
                 const int f = S.rf[r];
                 if (f < 0) bytes = 0;
                 src = rows + (size_t)max(f, 0) * fstride + (bytes ? x : 0);
                 dst = &S.A[b][r][4 * ch];
-            } else if (r < CC_ROWS + nsh) {
-                const int sh = r - CC_ROWS;
+            } else if (r < NR + nsh) {
+                const int sh = r - NR;
                 src = px + (size_t)(w.shell_lo + sh) * fstride + (bytes ? x : 0);
                 dst = &S.X[b][sh][4 * ch];
             } else {
-                const int sh = r - CC_ROWS - nsh;
+                const int sh = r - NR - nsh;
                 src = py + (size_t)(w.shell_lo + sh) * fstride + (bytes ? x : 0);
                 dst = &S.Y[b][sh][4 * ch];
             }
@@ -259,9 +246,9 @@ __global__ void __launch_bounds__(CC_THREADS, 2) k_contract_cc32(const float* __
         }
     };
 
-    float acc[4][4], hi[4][4], lo[4][4];
+    float acc[NI][4], hi[NI][4], lo[NI][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < NI; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = hi[i][j] = lo[i][j] = 0.f;
     if (nst > 0) load(0, 0);
@@ -287,13 +274,13 @@ __global__ void __launch_bounds__(CC_THREADS, 2) k_contract_cc32(const float* __
         __syncthreads();
 #pragma unroll 2
         for (int x = 0; x < C2_XS; x += 4) {
-            float4 a[4], q[4];
+            float4 a[NI], q[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(&S.A[b][ty + 16 * i][x]);
+            for (int i = 0; i < NI; ++i) a[i] = *reinterpret_cast<const float4*>(&S.A[b][ty + 16 * i][x]);
 #pragma unroll
             for (int j = 0; j < 4; ++j) q[j] = *reinterpret_cast<const float4*>(&S.P[x + j][4 * tx]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < NI; ++i) {
                 const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -306,7 +293,7 @@ __global__ void __launch_bounds__(CC_THREADS, 2) k_contract_cc32(const float* __
         }
         if (st & 1) {   // every 64 points: fold the block sums into the compensated pairs
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < NI; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     float s2, e2;
@@ -325,7 +312,39 @@ __global__ void __launch_bounds__(CC_THREADS, 2) k_contract_cc32(const float* __
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             slot[(size_t)(ty + 16 * i) * CC_COLS + 4 * tx + j] =
-                (double)acc[i][j] + (double)hi[i][j] + (double)lo[i][j];
+                i < NI ? (double)acc[i][j] + (double)hi[i][j] + (double)lo[i][j] : 0.0;
+}
+
+template <bool TWO, bool SYM>
+__global__ void __launch_bounds__(CC_THREADS, 2) k_contract_cc32(const float* __restrict__ rows,
+                                                                 const float* __restrict__ px,
+                                                                 const float* __restrict__ py, size_t fstride,
+                                                                 const Work* __restrict__ works,
+                                                                 const int2* __restrict__ pair_fields,
+                                                                 const int* __restrict__ row_fields, size_t npts,
+                                                                 size_t seg, double* __restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char c2_raw[];
+    Cc2Smem& S = *reinterpret_cast<Cc2Smem*>(c2_raw);
+    const Work w = works[blockIdx.x];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < CC_COLS; i += CC_THREADS) {
+        int2 v = {-1, -1};
+        if (i < w.npairs) {
+            v = pair_fields[w.pair0 + i];
+            v.x -= w.shell_lo;
+            v.y -= w.shell_lo;
+        }
+        S.pf[i] = v;
+    }
+    for (int i = tid; i < CC_ROWS; i += CC_THREADS) S.rf[i] = i < w.nrows ? row_fields[w.rowbase + i] : -1;
+    __syncthreads();
+    // row blocks of 16 that hold rows of this work (uniform over the CTA)
+    switch ((w.nrows + 15) >> 4) {
+        case 1: cc32_body<TWO, SYM, 1>(S, w, rows, px, py, fstride, npts, seg, partial); break;
+        case 2: cc32_body<TWO, SYM, 2>(S, w, rows, px, py, fstride, npts, seg, partial); break;
+        case 3: cc32_body<TWO, SYM, 3>(S, w, rows, px, py, fstride, npts, seg, partial); break;
+        default: cc32_body<TWO, SYM, 4>(S, w, rows, px, py, fstride, npts, seg, partial); break;
+    }
 }
 
 __global__ void k_reduce(const double* __restrict__ partial, int nsplit, size_t unit, int row_stride,

@@ -5,15 +5,14 @@ its own field-model draw (n_s in [-2, -1], f in [0.5, 0.9], sigma_g = 0.3),
 grid), l = 0, 2, 4: a 4962-vector per mock.
 
 The first six mocks of the ensemble go through the batch runner (CUDA
-graphs per size, autotuned schedule).  On the FP32 path every row must match
+graphs per size, autotuned schedule).  On both paths every row must match
 the FP64 oracle's multipoles of that mock at 1e-5 of max(|B|, rms_l), and the
 FP64 covariance of the rows must match the oracle's two-pass covariance of
-the oracle's rows.  The split-FP16 path is reported: on these fields (steeper
-spectra, n_s down to -2, and thin shells at low k) the tensor core's
-truncating FP32 accumulation (measured in test_gpu_mma_accumulation.py)
-takes its error to ~2.7e-5, which an emulation of that accumulation on the
-CPU reproduces (2.1e-5 on the worst mock); the bound below is that measured
-behaviour, not the parity gate.
+the oracle's rows.  These fields (steeper spectra, n_s down to -2, and thin
+shells at low k) are where the tensor core's truncating FP32 accumulation
+(measured in test_gpu_mma_accumulation.py) matters most: with accumulators
+drained every 256 points the split-FP16 rows of the second mock departed by
+2.3e-5; the library's 64-point default keeps them below 1e-5.
 """
 import numpy as np
 import pytest
@@ -70,7 +69,7 @@ def test_batch_rows_and_covariance_fullsize(ensemble, ora, prec):
     ok = scale > 0
     cov_err = float(np.max(np.abs(cov.cpu().numpy() - C_ora)[ok] / scale[ok]))
     print("batch %s: worst row gate %.3g, covariance error %.3g, tuning %s" % (prec, worst, cov_err, batch.tuning))
-    assert worst <= (1e-5 if prec == "fp32" else 5e-5)
+    assert worst <= 1e-5
     # each centred product carries two row errors (<= 1e-5 of the row scale),
     # and the scatter across mocks can sit below that scale: the same margin
     # as the small-grid batch test, 50 x the row gate
