@@ -259,17 +259,26 @@ __device__ __forceinline__ void cc32_body(Cc2Smem& S, const Work& w, const float
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        // pair products of this stage, P[x][p]
-        for (int e = tid; e < CC_COLS * C2_XS; e += CC_THREADS) {
-            const int p = e % CC_COLS, x = e / CC_COLS;
+        // pair products of this stage, P[x][p]: four consecutive points of one
+        // pair per thread (16-byte reads of the staged rows; lanes take
+        // consecutive pairs, so the column writes hit distinct banks)
+        for (int e = tid; e < CC_COLS * (C2_XS / 4); e += CC_THREADS) {
+            const int p = e % CC_COLS, x0 = 4 * (e / CC_COLS);
             const int2 bc = S.pf[p];
-            float v = 0.f;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
             if (bc.x >= 0) {
-                if (!TWO) v = S.X[b][bc.x][x] * S.X[b][bc.y][x];
-                else if (!SYM) v = S.X[b][bc.x][x] * S.Y[b][bc.y][x];
-                else v = S.X[b][bc.x][x] * S.Y[b][bc.y][x] + S.Y[b][bc.x][x] * S.X[b][bc.y][x];
+                const float4 xb = *reinterpret_cast<const float4*>(&S.X[b][bc.x][x0]);
+                const float4 rc = *reinterpret_cast<const float4*>(TWO ? &S.Y[b][bc.y][x0] : &S.X[b][bc.y][x0]);
+                v[0] = xb.x * rc.x; v[1] = xb.y * rc.y; v[2] = xb.z * rc.z; v[3] = xb.w * rc.w;
+                if (SYM) {
+                    const float4 yb = *reinterpret_cast<const float4*>(&S.Y[b][bc.x][x0]);
+                    const float4 xc = *reinterpret_cast<const float4*>(&S.X[b][bc.y][x0]);
+                    v[0] = fmaf(yb.x, xc.x, v[0]); v[1] = fmaf(yb.y, xc.y, v[1]);
+                    v[2] = fmaf(yb.z, xc.z, v[2]); v[3] = fmaf(yb.w, xc.w, v[3]);
+                }
             }
-            S.P[x][p] = v;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) S.P[x0 + u][p] = v[u];
         }
         __syncthreads();
 #pragma unroll 2
